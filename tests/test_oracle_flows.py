@@ -1,0 +1,142 @@
+"""Whole-step pins of the oracle against analytic flows and the paper's tables.
+
+* free-stream preservation on the skewed theta = 60 deg mesh;
+* steady power-law Poiseuille flow (textbook closed form), n < 1, = 1, > 1;
+* Taylor-Green vortex decay rate for n = 1 (exact Navier-Stokes solution);
+* second-order grid convergence of that decay rate;
+* the primary-eddy centre of the paper's Table 2 (slow; loose tolerance).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+def test_free_stream_preserved_on_skewed_mesh():
+    """Uniform (u, P) with walls moving at that velocity is a fixed point:
+    every difference of a constant vanishes and the boundary rule returns
+    the state itself (Eqs. (3.6)-(3.7), Sec. 4 boundary)."""
+    g = O.cavity_grid(17, 15, 1.0, 1.0, 60.0)
+    u0, v0, p0 = 0.04, -0.03, 2e-3
+    for side in g.wall_u:
+        n = len(g.wall_u[side][0])
+        g.wall_u[side] = (np.full(n, u0), np.full(n, v0))
+    prm = O.Params(dt=0.5 / 16, K=0.002, n=0.75, gamma_min=1e-4, eta_b=0.5)
+    shape = (g.ny, g.nx)
+    fhat, lam = O.initial_state(g, prm, np.full(shape, p0), np.full(shape, u0), np.full(shape, v0))
+    f0 = fhat.copy()
+    for _ in range(100):
+        fhat, lam = O.step(fhat, lam, g, prm)
+    assert np.abs(fhat - f0).max() < 1e-14
+
+
+def _poiseuille(n, ny, mu_wall=0.005, umax=0.05, ntau=2.0, eta_b=0.5):
+    """Channel periodic in x with a pressure drop, walls at y = 0 and y = H = 1.
+
+    Steady power-law solution (textbook): with G = -dP/dx,
+    u(y) = U_max [1 - |2 y / H - 1|^((n+1)/n)],
+    U_max = n/(n+1) (G/K)^(1/n) (H/2)^((n+1)/n).
+
+    K is set so that the apparent viscosity at the wall is mu_wall; the
+    kinetic model recovers the Navier-Stokes limit only while the mean free
+    path lam c = 3 mu / c stays well below H, so mu is kept small (the
+    zero-shear clamp caps it at the centreline for n < 1). The run starts
+    from the analytic profile and advances two viscous time constants
+    H^2 / (pi^2 mu_wall): a wrong viscosity, exponent or stress would drift
+    the profile away by tens of percent over that time.
+    Returns (max error / U_max, last GRE(u)).
+    """
+    H = 1.0
+    gdot_wall = umax * (n + 1) / n * 2.0 / H
+    K = mu_wall / gdot_wall ** (n - 1.0)
+    G = K * (umax * (n + 1) / n) ** n / (H / 2) ** (n + 1)
+    nx = 5
+    deta = H / (ny - 1)
+    Lx = nx * deta                      # square cells
+    g = O.periodic_grid(nx, ny, Lx, H, periodic_eta=False)
+    g.jump_P = -G * Lx
+    prm = O.Params(dt=0.5 * deta, K=K, n=n, gamma_min=0.01 * gdot_wall, eta_b=eta_b)
+    exact = umax * (1.0 - np.abs(2 * g.y / H - 1.0) ** ((n + 1) / n))
+    fhat, lam = O.initial_state(g, prm, P0=-G * g.x, ux0=exact)
+    nsteps = int(ntau * H * H / (np.pi ** 2 * mu_wall) / prm.dt)
+    run = O.Run(g=g, prm=prm, fhat=fhat, lam=lam)
+    run.advance(nsteps - 1)
+    run.advance(1, record=True)
+    ux, uy, _ = O.macros(run.fhat)
+    return np.abs(ux - exact).max() / umax, np.abs(uy).max(), run.history[-1][0]
+
+
+@pytest.mark.parametrize("n,tol33", [(0.5, 2.5e-2), (1.0, 5e-3), (1.5, 1e-2)])
+def test_power_law_poiseuille_profile_and_convergence(n, tol33):
+    e17, _, _ = _poiseuille(n, 17)
+    e33, v33, gre = _poiseuille(n, 33)
+    assert e33 < tol33, (e17, e33)
+    assert e17 / e33 > 2.5, (e17, e33)
+    assert v33 < 1e-6 * 0.05
+    assert gre < 1e-6
+
+
+def _taylor_green(N, nu=0.002, U0=0.01, t_end=1.0, t_start=0.25, eta_b=0.5):
+    """Doubly periodic Taylor-Green vortex on [0, 1)^2 with k = 2 pi, n = 1:
+    u = -U0 cos(kx) sin(ky) e^{-2 nu k^2 t}, v = U0 sin(kx) cos(ky) e^{...},
+    P = -U0^2/4 (cos 2kx + cos 2ky) e^{-4 nu k^2 t} (exact NSE solution).
+
+    The viscosity is small enough that the kinetic correction (lam c k)^2
+    stays below 0.2 %. Returns the measured and the exact decay rate of the
+    velocity amplitude over [t_start, t_end]."""
+    k = 2 * np.pi
+    g = O.periodic_grid(N, N, 1.0, 1.0, periodic_eta=True)
+    dt = 0.5 / N
+    prm = O.Params(dt=dt, K=nu, n=1.0, gamma_min=1e-8, eta_b=eta_b)
+    x, y = g.x, g.y
+    mode_u = -np.cos(k * x) * np.sin(k * y)
+    mode_v = np.sin(k * x) * np.cos(k * y)
+    P0 = -U0 ** 2 / 4 * (np.cos(2 * k * x) + np.cos(2 * k * y))
+    fhat, lam = O.initial_state(g, prm, P0, U0 * mode_u, U0 * mode_v)
+
+    def amp(f):
+        ux, uy, _ = O.macros(f)
+        return np.sum(ux * mode_u + uy * mode_v) / np.sum(mode_u ** 2 + mode_v ** 2)
+
+    n1, n2 = int(round(t_start / dt)), int(round(t_end / dt))
+    for s in range(n2):
+        if s == n1:
+            a1 = amp(fhat)
+        fhat, lam = O.step(fhat, lam, g, prm)
+    measured = math.log(a1 / amp(fhat)) / ((n2 - n1) * dt)
+    return measured, 2 * nu * k * k
+
+
+def test_taylor_green_decay_rate_newtonian():
+    """Viscous decay rate 2 nu k^2 with nu = lam c_s^2 = K (Eq. (2.14), n = 1)."""
+    measured, exact = _taylor_green(64)
+    assert abs(measured / exact - 1) < 0.015, (measured, exact)
+
+
+@pytest.mark.parametrize("eta_b", [0.5, 1.0])
+def test_taylor_green_second_order_convergence(eta_b):
+    """The decay-rate error falls by at least 3x per halving of h (2nd order)."""
+    e = [abs(m / x - 1) for m, x in (_taylor_green(N, eta_b=eta_b) for N in (32, 64))]
+    assert e[0] / e[1] > 3.0, e
+
+
+@pytest.mark.slow
+def test_primary_eddy_centre_table2(golden_dir):
+    """Table 2 (theta = 60 deg, n = 0.75, Re = 100): primary eddy at
+    (1.4292, 0.6872). On a 33^2 grid the psi-minimum node must lie within
+    1.5 grid spacings (physical) of the printed centre."""
+    rows = np.loadtxt(os.path.join(golden_dir, "eddy_centres_re100.txt"))
+    row = rows[(rows[:, 0] == 60) & (rows[:, 1] == 0.75)][0]
+    run = O.cavity_run(33, 100.0, 0.75, theta_deg=60.0)
+    while run.steps < 40000:
+        run.advance(500, record=True)
+        if run.history[-1][0] < 1e-8:
+            break
+    psi = run.fields()["psi"]
+    j, i = np.unravel_index(np.argmin(psi), psi.shape)
+    x, y = run.g.x[j, i], run.g.y[j, i]
+    h = 1.0 / 32
+    assert abs(x - row[2]) < 1.5 * h * (1 + 2 / math.sqrt(3)) and abs(y - row[3]) < 1.5 * h
