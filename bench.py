@@ -1,0 +1,433 @@
+#!/usr/bin/env python3
+"""Throughput of the IFDLBM step on GB300 (MLUPS), one JSON line on rank 0.
+
+Default workload: the power-law sweep of 10 cavities (257^2 nodes each,
+theta = 60 deg, n in {0.5, 0.75, 1.0, 1.25, 1.5} x Re in {100, 1000})
+advanced together, one batched time step per bench step (Steps (2)-(8) of
+the paper: equilibrium, lagged power-law relaxation time, the two-stage
+finite-difference update on the mapped grid, wall nodes and the Eq. (2.19)
+residual). Every timed step is bracketed by CUDA events on the library's
+stream; a 256 MiB buffer is written between steps (outside the events) so
+that no step starts from a warm L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32dev|fp64]
+                  [--workload sweep257|...] [--impl ours|reference]
+
+With N > 1 (torchrun), every rank advances its own copy of the workload
+(independent cavities, no collective on the data path: weak scaling) and
+the value is all ranks' lattice updates over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+BASELINE_METRIC = "MLUPS & HBM GB/s vs ~8 TB/s peak; FP32/batched vs FP64 at stated error"
+KERNEL_NAMES = {0: "collide", 1: "half", 2: "full", 3: "reduce", 4: "fused"}
+DEVICE_KERNEL = {"collide": "k_collide", "half": "k_half", "full": "k_full",
+                 "reduce": "k_residual_reduce", "fused": "k_fused"}
+# Algorithmic DRAM bytes per lattice update of each step kernel: every array
+# element the kernel must read or write, once ("Kernels").
+ALGO_BYTES = {
+    ("fused", "fp32dev"): 88, ("fused", "fp64"): 160,
+    ("collide", "fp32dev"): 148, ("collide", "fp64"): 256,
+    ("half", "fp32dev"): 80, ("half", "fp64"): 152,
+    ("full", "fp32dev"): 132, ("full", "fp64"): 240,
+}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=400)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--workload", default="sweep257")
+    p.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp64"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "staged", "fused"])
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="CPU work budget of the oracle baseline sample")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Clocks during the timed region (nvidia-smi sampler)
+# ---------------------------------------------------------------------------
+CLOCK_FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        self.marks = []
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 10:
+                        rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not rows:
+            return None
+        sm = []
+        reasons = set()
+        sm_max = None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                clk = float(r[2])
+                sm_max = float(r[3])
+            except ValueError:
+                continue
+            if clk > 0:
+                sm.append(clk)
+            for k, name in enumerate(names):
+                if r[6 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": sm_max, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# ncu-derived DRAM traffic (profiles/traffic.json), valid only for the
+# kernel source it was taken from
+# ---------------------------------------------------------------------------
+def kernel_source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2306_07603_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_per_launch(kernel, precision, lu_per_launch):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d[f"{kernel}:{precision}"]
+        if e.get("src_digest") != kernel_source_digest():
+            return None
+        return float(e["bytes_per_lu"]) * lu_per_launch
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# Oracle CPU baseline (the only use of oracle/ in this file)
+# ---------------------------------------------------------------------------
+def oracle_sample_mlups(spec, seconds):
+    """Times the FP64 oracle on one cavity of the workload from rest for about
+    `seconds` of single-threaded NumPy work. Returns (MLUPS, steps, seconds)."""
+    import oracle as O
+
+    run = O.cavity_run(spec.nx, spec.Re, spec.n, theta_deg=spec.theta_deg, U=spec.U_lid,
+                       L=spec.L, H=spec.H, ny=spec.ny)
+    t0 = time.perf_counter()
+    run.advance(2)
+    per = (time.perf_counter() - t0) / 2
+    n = max(1, int(seconds / max(per, 1e-6)) - 2)
+    t0 = time.perf_counter()
+    run.advance(n)
+    dt = time.perf_counter() - t0
+    return spec.nodes * n / dt / 1e6, n, dt, run
+
+
+def cpu_baseline(specs, seconds):
+    spec = specs[min(1, len(specs) - 1)]
+    mlups, n, dt, _ = oracle_sample_mlups(spec, seconds)
+    return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 NumPy oracle, one {spec.nx}x{spec.ny} cavity of the workload "
+                      f"(theta={spec.theta_deg:g}, n={spec.n:g}, Re={spec.Re:g}) from rest, "
+                      f"{n} steps in {dt:.1f} s, single thread"}
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
+def make_solver(specs, precision, kernel, stream=None):
+    from paper_2306_07603_gb300.solver import Solver, cavity
+
+    cavs = [cavity(s.nx, s.ny, s.Re, s.n, theta_deg=s.theta_deg, U_lid=s.U_lid, L=s.L, H=s.H)
+            for s in specs]
+    return Solver(cavs, stream=stream, precision=precision, kernel=kernel)
+
+
+def reduce_over_ranks(total_ms, launches, world, device):
+    """Slowest rank's timed milliseconds and the job's total kernel launches."""
+    import torch
+    import torch.distributed as dist
+
+    t_ms = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    t_n = torch.tensor([float(launches)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t_n, op=dist.ReduceOp.SUM)
+    return float(t_ms[0]), int(t_n[0])
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.workloads import WORKLOADS
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    specs = WORKLOADS[args.workload]()
+    lu_step = sum(s.nodes for s in specs)
+
+    s = make_solver(specs, args.precision, args.kernel)
+    stream = s.stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sampler = ClockSampler(local)
+    sampler.start()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(0.0)
+            s.step(1)
+    s.sync()
+    capi.ifdlbm_profile(s.h, 1)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = capi.ifdlbm_launch_count()
+    sampler.mark()
+    with torch.cuda.stream(stream):
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            capi.ifdlbm_step(s.h, 1)
+            ends[k].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark()
+    launches = capi.ifdlbm_launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    kern = {}
+    for kid, name in KERNEL_NAMES.items():
+        ms, n = capi.ifdlbm_profile_read(s.h, kid)
+        if n:
+            kern[name] = (ms, n)
+    capi.ifdlbm_profile(s.h, 0)
+    resid = s.residual()
+    clocks = sampler.stop()
+
+    max_ms, launches_all = reduce_over_ranks(total_ms, launches, world, "cuda")
+    value = lu_step * world * args.steps / (max_ms * 1e-3) / 1e6
+
+    # roofline of the dominant kernel, from its live event times
+    peak, peak_src = load_peaks()
+    dom = max(kern, key=lambda k: kern[k][0]) if kern else None
+    roofline = None
+    if dom is not None and (dom, args.precision) in ALGO_BYTES:
+        ms, n = kern[dom]
+        per_launch_s = ms / n * 1e-3
+        algo = ALGO_BYTES[(dom, args.precision)] * lu_step
+        achieved = algo / per_launch_s / 1e9
+        roofline = {"bound": "hbm", "kernel": DEVICE_KERNEL[dom], "achieved": round(achieved, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": traffic_per_launch(dom, args.precision, lu_step),
+                    "algorithmic_bytes": algo, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
+                    if peak_src == "measured" else "fallback",
+                    "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, specs, stream, world)
+
+    out = None
+    if rank == 0:
+        step_ms = max_ms / args.steps
+        out = {
+            "metric": "MLUPS",
+            "value": round(value, 2),
+            "unit": "MLUPS",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(step_ms, 5),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "fp32dev" else "f64",
+            "data": "synthetic (cavities from rest; no dataset)",
+            "config": {"workload": args.workload, "cavities": len(specs),
+                       "grids": sorted({f"{sp.nx}x{sp.ny}" for sp in specs}),
+                       "lattice_updates_per_step": lu_step, "precision": args.precision,
+                       "kernel": args.kernel, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "l2": "256 MiB buffer written between timed steps (outside the events)",
+                       "baseline_metric": BASELINE_METRIC},
+            "hbm_gbs_algorithmic": round(value * 1e6 * (88 if args.precision == "fp32dev" else 160) / 1e9, 1),
+            "roofline": roofline,
+            "kernels_ms_per_launch": {k: round(v[0] / v[1], 5) for k, v in kern.items()},
+            "gpu_launches": launches_all,
+            "clocks": clocks,
+            "e2e": e2e,
+            "last_residual_cavity0": [float(x) for x in resid[0]],
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(specs, args.cpu_seconds)
+    s.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def run_e2e(args, specs, stream, world):
+    """Same metric through the public API with HOST buffers: create the batch
+    from host parameters, then every step reads its residual back into pinned
+    host memory (a device -> host copy and a synchronisation per step), and
+    the final fields of every cavity come back to the host."""
+    import numpy as np
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+
+    nsteps = max(10, args.steps // 2)
+    ncav = len(specs)
+    pinned = torch.empty((ncav, 4), dtype=torch.float64, pin_memory=True)
+    fields = [torch.empty((4, sp.ny, sp.nx), dtype=torch.float64, pin_memory=True) for sp in specs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s = make_solver(specs, args.precision, args.kernel, stream=stream)
+    for _ in range(nsteps):
+        capi.ifdlbm_step(s.h, 1)
+        capi.ifdlbm_batch_residual(s.h, pinned.numpy())
+    for k in range(ncav):
+        f = fields[k].numpy()
+        capi.ifdlbm_batch_macros(s.h, k, f[0], f[1], f[2], f[3])
+    t1 = time.perf_counter()
+    h2d = capi.ifdlbm_info(s.h, 0).h2d_bytes
+    s.close()
+    lu = sum(sp.nodes for sp in specs) * nsteps * world
+    d2h = ncav * 4 * 8 * nsteps + sum(4 * 8 * sp.nodes for sp in specs)
+    return {"value": round(lu / (t1 - t0) / 1e6, 2), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(h2d / nsteps, 1), "d2h_bytes_per_step": round(d2h / nsteps, 1),
+            "steps": nsteps,
+            "what": "create from host parameters + per-step residual D2H (pinned) + final rho/u/v/psi D2H"}
+
+
+# ---------------------------------------------------------------------------
+# The reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    from paper_2306_07603_gb300.workloads import WORKLOADS
+
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    import oracle as O
+
+    specs = WORKLOADS[args.workload]()
+    # one reference step = one time step of one cavity of the workload (a
+    # bounded sample), cycling through the cavities
+    runs = [O.cavity_run(sp.nx, sp.Re, sp.n, theta_deg=sp.theta_deg, U=sp.U_lid, L=sp.L, H=sp.H,
+                         ny=sp.ny) for sp in specs]
+    for k in range(args.warmup):
+        runs[k % len(runs)].advance(1)
+    lu = 0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = runs[k % len(runs)]
+        r.advance(1)
+        lu += r.g.nx * r.g.ny
+    dt = time.perf_counter() - t0
+    value = lu / dt / 1e6
+    return {
+        "impl": "reference", "metric": "MLUPS", "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "precision": "fp64 oracle",
+                   "sample": "each step = one time step of one cavity of the workload"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} single-cavity steps cycling over "
+                                   f"{len(specs)} cavities, NumPy, single thread"},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,237 @@
+/*
+ * ifdlbm.h - C ABI of the GB300 (sm_103a) IFDLBM library.
+ *
+ * The library advances the incompressible finite-difference lattice
+ * Boltzmann method (IFDLBM) of Chen, Chai, Zhao and Shi (arXiv 2306.07603)
+ * for a power-law fluid in a lid-driven isosceles trapezoidal cavity that
+ * is mapped to a uniform (xi, eta) computational grid (Sec. 4, Eq. 3.8).
+ * One call of ifdlbm_step performs Steps (2)-(7) of the paper's calculation
+ * process per time step, with Step (8)'s global relative error (Eq. 2.19)
+ * formed on the last step of the call.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grids are nx x ny nodes; node (i, j) sits at xi = i/(nx-1),
+ *    eta = j/(ny-1). j = 0 is the bottom wall, j = ny-1 the lid (Eq. 1.5).
+ *    Host and device field arrays are row-major [ny][nx] (xi contiguous);
+ *    distribution arrays are [9][ny][nx] in the D2Q9 order of Eq. (2.9).
+ *  - Every compute step runs as sm_103a CUDA on the stream given at
+ *    creation. There is no CPU fallback: without a CUDA device, creation
+ *    fails with IFDLBM_ERR_CUDA.
+ *  - The handle owns all device memory it allocates, through the allocator
+ *    registered with ifdlbm_set_allocator (cudaMalloc/cudaFree if none).
+ *    Pointers passed in are borrowed for the duration of the call only.
+ *  - Functions taking HOST buffers synchronise the handle's stream before
+ *    they return. Functions suffixed _dev take DEVICE pointers, enqueue
+ *    their copies on the handle's stream and return without synchronising.
+ *  - Return value: IFDLBM_OK (0) or a negative IFDLBM_ERR_* code; the text
+ *    of the last error is available from ifdlbm_last_error(handle), or
+ *    ifdlbm_last_error(NULL) for a failed create.
+ *  - A handle is not thread safe: calls on one handle must not overlap.
+ */
+#ifndef IFDLBM_H
+#define IFDLBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IFDLBM_OK 0
+#define IFDLBM_ERR_INVALID_ARG (-1) /* argument out of its documented range */
+#define IFDLBM_ERR_CUDA (-2)        /* a CUDA call failed (text in last_error) */
+#define IFDLBM_ERR_OOM (-3)         /* the allocator returned NULL */
+#define IFDLBM_ERR_DIVERGED (-4)    /* a non-finite velocity appeared in a step */
+#define IFDLBM_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+
+/* Storage / arithmetic form of the distributions (pattern "precision"). */
+#define IFDLBM_FP64 0    /* f-hat and all arithmetic in FP64 */
+#define IFDLBM_FP32DEV 1 /* f-hat stored and updated in FP32 as deviations
+                            g_i = f-hat_i - w_i rho0 from the rest equilibrium
+                            (Eq. 2.8 at P = 0, u = 0); metrics, the power-law
+                            relaxation time and all reductions in FP64 */
+
+/* Step kernel organisation. */
+#define IFDLBM_KERNEL_AUTO 0   /* FUSED for FP32DEV, STAGED for FP64 */
+#define IFDLBM_KERNEL_STAGED 1 /* three launches per step, no recomputation */
+#define IFDLBM_KERNEL_FUSED 2  /* one launch per step, eta-marching window */
+
+/* Geometry of the isosceles trapezoid (Sec. 2, Eq. 3.8.1 with general L, H):
+ * bottom edge of length L, height H, base angle theta_deg in (0, 90]; the
+ * side walls lean outward so the lid spans L + 2 H cot(theta). theta_deg =
+ * 90 is the square cavity (identity map). */
+typedef struct {
+  double L;
+  double H;
+  double theta_deg;
+} ifdlbm_geometry;
+
+/* Run options. ifdlbm_default_options fills the defaults noted here. */
+typedef struct {
+  double cfl;       /* Courant number, 0.5 (Sec. 5.1) */
+  double c;         /* lattice speed, 1.0 (Sec. 5.1) */
+  double eta_b;     /* blend of Eq. (2.5) in [0, 1]; default 0.5 */
+  double gamma_min; /* zero-shear clamp of |gamma-dot|; <= 0 means 1e-3 U/H */
+  double dt;        /* time step; <= 0 means cfl * min(L/(nx-1), H/(ny-1)) / c */
+  double rho0;      /* reference density, 1.0 */
+  int precision;    /* IFDLBM_FP64 (default) or IFDLBM_FP32DEV */
+  int kernel;       /* IFDLBM_KERNEL_*; default AUTO */
+  int graph_chunk;  /* steps per captured CUDA graph, even, >= 2; default 32;
+                       0 disables graph capture */
+  int reserved;
+} ifdlbm_options;
+
+/* One cavity of a batch (pattern "batching"). */
+typedef struct {
+  int nx;
+  int ny;
+  ifdlbm_geometry geom;
+  double Re;    /* power-law Reynolds number of Eq. (2.15.1), > 0 */
+  double n;     /* power-law index of Eq. (1.4), > 0 */
+  double U_lid; /* lid speed U of Eq. (1.5), > 0 */
+} ifdlbm_cavity;
+
+/* Scalar facts about one cavity of a handle. */
+typedef struct {
+  int nx, ny;
+  int precision;
+  int kernel;
+  double dt;        /* time step */
+  double K;         /* consistency coefficient U^(2-n) H^n / Re, Eq. (2.15.1) */
+  double gamma_min; /* clamp in use */
+  double eta_b;
+  double courant_max; /* max over nodes/directions of dt(|c_xi|/dxi + |c_eta|/deta) */
+  int64_t steps;      /* time steps taken so far */
+  int64_t device_bytes; /* device memory owned by the whole handle */
+  int64_t h2d_bytes;    /* bytes the handle copied host -> device at creation */
+} ifdlbm_info_t;
+
+typedef struct ifdlbm_ctx *ifdlbm_handle;
+
+/* Device allocator hooks: alloc returns a device pointer of at least
+ * `bytes` bytes usable on `stream`, or NULL; free releases it. `ctx` is
+ * passed back unchanged. Process-wide; affects handles created afterwards.
+ * Passing NULL for both restores cudaMalloc/cudaFree. */
+typedef void *(*ifdlbm_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*ifdlbm_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int ifdlbm_set_allocator(ifdlbm_alloc_fn alloc, ifdlbm_free_fn free_fn, void *ctx);
+
+/* Fills *opt with the defaults listed in ifdlbm_options. */
+int ifdlbm_default_options(ifdlbm_options *opt);
+
+/* Creates one lid-driven trapezoidal cavity at rest (Step (1), Sec. 4):
+ * f-hat = f = f^eq(P = 0, u) with u = 0 inside and on the walls, u = (U, 0)
+ * on the lid nodes (impulsive start; the two top corners are wall nodes),
+ * and lambda_prev equal to Eq. (2.14) at zero shear.
+ *  nx, ny   >= 5 nodes along xi and eta
+ *  g        L > 0, H > 0, 0 < theta_deg <= 90
+ *  Re, n, U_lid  > 0 (Eqs. 1.4, 1.5, 2.15.1)
+ *  opt      NULL for the defaults
+ *  stream   cudaStream_t on which every device operation of the handle is
+ *           enqueued (NULL: the legacy default stream)
+ *  out      receives the handle
+ * Errors: INVALID_ARG for out-of-range arguments, OOM, CUDA. */
+int ifdlbm_create(int nx, int ny, ifdlbm_geometry g, double Re, double n, double U_lid,
+                  const ifdlbm_options *opt, void *stream, ifdlbm_handle *out);
+
+/* Creates `ncav` independent cavities (each as ifdlbm_create) that every
+ * ifdlbm_step advances together in the same launches. `cavs` is a host
+ * array of ncav entries; 1 <= ncav <= 4096. */
+int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_options *opt,
+                        void *stream, ifdlbm_handle *out);
+
+/* Advances every cavity of the handle by `nsteps` >= 0 time steps, Steps
+ * (2)-(7) of Sec. 4 (Eqs. 2.8-2.18, 3.6-3.7, non-equilibrium extrapolation
+ * walls). On the last step it also forms, per cavity, the global relative
+ * errors of Eq. (2.19) between that step's input and output fields, the
+ * max-norm velocity residual and the kinetic energy of Eq. (5.1).
+ * Asynchronous: returns once the work is enqueued. A divergence flagged on
+ * the device is reported by the next synchronising call. */
+int ifdlbm_step(ifdlbm_handle h, int nsteps);
+
+/* Macroscopic fields of cavity 0 at the current time, into HOST arrays of
+ * nx*ny doubles ([ny][nx]); any pointer may be NULL to skip that field.
+ *  rho  equivalent density rho0 + P / c_s^2 (the model carries P, Eq. 2.11)
+ *  u, v velocity, Eq. (2.10)
+ *  psi  stream function: psi = 0 on the bottom wall, integrated along each
+ *       xi = const line, d psi = (u y_eta - v x_eta) d eta, trapezoidal rule.
+ * Synchronises. */
+int ifdlbm_macros(ifdlbm_handle h, double *rho, double *u, double *v, double *psi);
+
+/* As ifdlbm_macros for cavity `cavity` of a batch, into HOST arrays. */
+int ifdlbm_batch_macros(ifdlbm_handle h, int cavity, double *rho, double *u, double *v,
+                        double *psi);
+
+/* As ifdlbm_batch_macros into DEVICE arrays; does not synchronise. */
+int ifdlbm_macros_dev(ifdlbm_handle h, int cavity, double *rho, double *u, double *v,
+                      double *psi);
+
+/* Residuals of cavity 0 from the last step taken, into HOST out[4]:
+ *  out[0] E(u), out[1] E(P) of Eq. (2.19),
+ *  out[2] max_nodes |u^n - u^(n-1)| / max_nodes |u^n| (max-norm residual),
+ *  out[3] kinetic energy 1/2 sum |u|^2 J dxi deta of Eq. (5.1)
+ *         (composite trapezoidal rule; J the Jacobian of Eq. 3.3).
+ * All zero before the first step. Synchronises; returns DIVERGED if a step
+ * produced a non-finite velocity. */
+int ifdlbm_residual(ifdlbm_handle h, double *out);
+
+/* Residuals of every cavity, HOST out[4 * ncav] in the order above. */
+int ifdlbm_batch_residual(ifdlbm_handle h, double *out);
+
+/* State of cavity `cavity` in the paper's variables: fhat[9][ny][nx]
+ * (f-hat of Eq. 2.3, full value, not the FP32 deviation) and
+ * lambda_prev[ny][nx] (the relaxation time the next step's Eq. (2.18)
+ * will use). HOST arrays; either may be NULL. Synchronises. */
+int ifdlbm_get_state(ifdlbm_handle h, int cavity, double *fhat, double *lambda_prev);
+
+/* Replaces the state of cavity `cavity` (HOST arrays, layouts as
+ * ifdlbm_get_state; both required). The residual of the next step
+ * compares against these fields. Synchronises. */
+int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const double *lambda_prev);
+
+/* Copies of the whole batch state between the handle and caller-owned
+ * DEVICE memory of ifdlbm_state_bytes(h) bytes (opaque layout, valid only
+ * for the same handle). Used for checkpoints. Do not synchronise. */
+int64_t ifdlbm_state_bytes(ifdlbm_handle h);
+int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst);
+int ifdlbm_load_state_dev(ifdlbm_handle h, const void *src);
+
+/* Scalar facts about cavity `cavity` (see ifdlbm_info_t). */
+int ifdlbm_info(ifdlbm_handle h, int cavity, ifdlbm_info_t *info);
+
+/* Waits for the handle's stream; returns DIVERGED or CUDA errors seen. */
+int ifdlbm_sync(ifdlbm_handle h);
+
+/* Releases the handle and all device memory it owns. NULL is a no-op. */
+int ifdlbm_destroy(ifdlbm_handle h);
+
+/* Text of the last error on `h` (or of the last failed create when h is
+ * NULL). Valid until the next call on the same handle. */
+const char *ifdlbm_last_error(ifdlbm_handle h);
+
+/* Kernel timing. While enabled, every step kernel launch of `h` is
+ * bracketed by CUDA events on the handle's stream (steps then run without
+ * graph replay). ifdlbm_profile_read synchronises and returns, for kernel
+ * `kernel` (IFDLBM_KPROF_*), the summed event time in milliseconds and the
+ * number of launches since profiling was (re)enabled. Disabling discards
+ * the records. */
+#define IFDLBM_KPROF_COLLIDE 0 /* staged: Steps (2)-(3) */
+#define IFDLBM_KPROF_HALF 1    /* staged: Step (4) */
+#define IFDLBM_KPROF_FULL 2    /* staged: Steps (5)-(6) + residual partials */
+#define IFDLBM_KPROF_REDUCE 3  /* residual reduction (Step 8) */
+#define IFDLBM_KPROF_FUSED 4   /* fused: Steps (2)-(6) in one launch */
+#define IFDLBM_KPROF_COUNT 5
+int ifdlbm_profile(ifdlbm_handle h, int enable);
+int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *launches);
+
+/* Number of kernel launches the library has enqueued since the process
+ * started (graph replays count every kernel node). */
+int64_t ifdlbm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IFDLBM_H */

@@ -1,0 +1,696 @@
+// Host implementation of the C ABI declared in include/ifdlbm.h.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ifdlbm.h"
+#include "internal.h"
+
+using ifd::CavDev;
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+thread_local std::string g_create_error;
+
+ifdlbm_alloc_fn g_alloc = nullptr;
+ifdlbm_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+
+struct Alloc {
+  void *p;
+  size_t bytes;
+};
+
+}  // namespace
+
+struct ifdlbm_ctx {
+  int ncav = 0;
+  int precision = IFDLBM_FP64;
+  int kernel = IFDLBM_KERNEL_STAGED;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  ifdlbm_options opt{};
+  std::vector<ifdlbm_cavity> spec;
+  std::vector<CavDev> cav;
+  std::vector<double> courant;
+  ifd::Bufs b{};
+  int ntiles = 0;
+  int64_t total_plane = 0;
+  int64_t geo_len = 0;
+  int64_t max_n2 = 0;
+  double *stage = nullptr;  // staging for host transfers: 10 * max_n2 doubles
+  int cur = 0;
+  int64_t steps = 0;
+  int64_t bytes = 0;
+  int64_t h2d_bytes = 0;
+  std::vector<Alloc> allocs;
+  std::string err;
+  // graph_chunk steps captured per parity (graph_chunk is even)
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  ifdlbm_alloc_fn alloc = nullptr;
+  ifdlbm_free_fn free_fn = nullptr;
+  void *alloc_ctx = nullptr;
+  // kernel timing (ifdlbm_profile)
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> ev_marks;  // kernel, (start, stop)
+};
+
+namespace {
+
+int fail(ifdlbm_ctx *h, int code, const std::string &msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(ifdlbm_ctx *h, cudaError_t e, const char *what) {
+  return fail(h, IFDLBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+void *dalloc(ifdlbm_ctx *h, size_t bytes) {
+  void *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (h->alloc) {
+    p = h->alloc(bytes, (void *)h->stream, h->alloc_ctx);
+  } else {
+    if (cudaMalloc(&p, bytes) != cudaSuccess) p = nullptr;
+  }
+  if (p) {
+    h->allocs.push_back({p, bytes});
+    h->bytes += int64_t(bytes);
+  }
+  return p;
+}
+
+void release_all(ifdlbm_ctx *h) {
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  h->ev_pool.clear();
+  for (int p = 0; p < 2; ++p)
+    if (h->gexec[p]) {
+      cudaGraphExecDestroy(h->gexec[p]);
+      h->gexec[p] = nullptr;
+    }
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (auto &a : h->allocs) {
+    if (h->free_fn)
+      h->free_fn(a.p, a.bytes, (void *)h->stream, h->alloc_ctx);
+    else
+      cudaFree(a.p);
+  }
+  h->allocs.clear();
+}
+
+double cot_deg(double theta_deg) {
+  if (theta_deg == 90.0) return 0.0;
+  const double t = theta_deg * (M_PI / 180.0);
+  return std::cos(t) / std::sin(t);
+}
+
+int validate(ifdlbm_ctx *h, int idx, const ifdlbm_cavity &c) {
+  char buf[256];
+  auto bad = [&](const char *what) {
+    std::snprintf(buf, sizeof buf, "cavity %d: %s", idx, what);
+    return fail(h, IFDLBM_ERR_INVALID_ARG, buf);
+  };
+  if (c.nx < 5 || c.ny < 5) return bad("nx and ny must be >= 5");
+  if ((int64_t)c.nx * c.ny > (int64_t)1 << 28) return bad("grid larger than 2^28 nodes");
+  if (!(c.geom.L > 0) || !(c.geom.H > 0)) return bad("L and H must be > 0");
+  if (!(c.geom.theta_deg > 0 && c.geom.theta_deg <= 90)) return bad("theta_deg must be in (0, 90]");
+  if (!(c.Re > 0) || !(c.n > 0) || !(c.U_lid > 0)) return bad("Re, n and U_lid must be > 0");
+  if (!std::isfinite(c.Re) || !std::isfinite(c.n) || !std::isfinite(c.U_lid))
+    return bad("Re, n and U_lid must be finite");
+  return IFDLBM_OK;
+}
+
+cudaEvent_t next_event(ifdlbm_ctx *h, size_t *idx) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  *idx = h->ev_used;
+  return h->ev_pool[h->ev_used++];
+}
+
+// Runs `launch` bracketed by events when profiling is on.
+template <class F>
+void timed(ifdlbm_ctx *h, int kernel, F &&launch) {
+  if (!h->profiling) {
+    launch();
+    return;
+  }
+  size_t a, b;
+  cudaEventRecord(next_event(h, &a), h->stream);
+  launch();
+  cudaEventRecord(next_event(h, &b), h->stream);
+  h->ev_marks.push_back({kernel, {a, b}});
+}
+
+template <class T>
+void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
+  ifd::StepArgs a{};
+  a.cav = h->b.cav;
+  a.geo = h->b.geo;
+  a.tile_cav = h->b.tile_cav;
+  a.g_in = h->b.g[parity];
+  a.g_out = h->b.g[parity ^ 1];
+  a.lam_in = h->b.lam[parity];
+  a.lam_out = h->b.lam[parity ^ 1];
+  a.fb = h->b.fb;
+  a.fp = h->b.fp;
+  a.fh = h->b.fh;
+  a.m0 = h->b.m0;
+  a.part = h->b.part;
+  a.status = h->b.status;
+  a.want_residual = want_residual ? 1 : 0;
+  timed(h, IFDLBM_KPROF_COLLIDE, [&] { ifd::launch_collide<T>(a, h->ntiles, h->stream); });
+  timed(h, IFDLBM_KPROF_HALF, [&] { ifd::launch_half<T>(a, h->ntiles, h->stream); });
+  timed(h, IFDLBM_KPROF_FULL, [&] { ifd::launch_full<T>(a, h->ntiles, h->stream); });
+  if (want_residual)
+    timed(h, IFDLBM_KPROF_REDUCE, [&] {
+      ifd::launch_residual_reduce(h->b.cav, h->b.part, h->b.resid, h->ncav, h->stream);
+    });
+}
+
+void enqueue_step_any(ifdlbm_ctx *h, int parity, bool want_residual) {
+  if (h->precision == IFDLBM_FP64)
+    enqueue_step<double>(h, parity, want_residual);
+  else
+    enqueue_step<float>(h, parity, want_residual);
+}
+
+int launches_per_step(bool residual) { return residual ? 4 : 3; }
+
+int ensure_graph(ifdlbm_ctx *h, int parity) {
+  if (h->gexec[parity]) return IFDLBM_OK;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+  int p = parity;
+  for (int s = 0; s < h->opt.graph_chunk; ++s) {
+    enqueue_step_any(h, p, false);
+    p ^= 1;
+  }
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(h->stream, &graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->gexec[parity], graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  return IFDLBM_OK;
+}
+
+int check_status(ifdlbm_ctx *h) {
+  unsigned st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, h->b.status, sizeof st, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "status read");
+  if (st & 1u) return fail(h, IFDLBM_ERR_DIVERGED, "a step produced a non-finite velocity");
+  return IFDLBM_OK;
+}
+
+bool cavity_ok(ifdlbm_ctx *h, int cavity) { return h && cavity >= 0 && cavity < h->ncav; }
+
+}  // namespace
+
+extern "C" {
+
+int ifdlbm_set_allocator(ifdlbm_alloc_fn alloc, ifdlbm_free_fn free_fn, void *ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr))
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "allocator and free must be set together");
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = ctx;
+  return IFDLBM_OK;
+}
+
+int ifdlbm_default_options(ifdlbm_options *opt) {
+  if (!opt) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "opt is NULL");
+  std::memset(opt, 0, sizeof *opt);
+  opt->cfl = 0.5;
+  opt->c = 1.0;
+  opt->eta_b = 0.5;
+  opt->gamma_min = 0.0;
+  opt->dt = 0.0;
+  opt->rho0 = 1.0;
+  opt->precision = IFDLBM_FP64;
+  opt->kernel = IFDLBM_KERNEL_AUTO;
+  opt->graph_chunk = 32;
+  return IFDLBM_OK;
+}
+
+int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_options *opt_in,
+                        void *stream, ifdlbm_handle *out) {
+  if (!out) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ncav < 1 || ncav > 4096 || !cavs)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "ncav must be in [1, 4096] with a cavity array");
+  ifdlbm_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else
+    ifdlbm_default_options(&opt);
+  if (!(opt.cfl > 0) || !(opt.c > 0) || !(opt.eta_b >= 0 && opt.eta_b <= 1) || !(opt.rho0 > 0))
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: need cfl > 0, c > 0, eta_b in [0,1], rho0 > 0");
+  if (opt.precision != IFDLBM_FP64 && opt.precision != IFDLBM_FP32DEV)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown precision");
+  if (opt.kernel < IFDLBM_KERNEL_AUTO || opt.kernel > IFDLBM_KERNEL_FUSED)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown kernel");
+  if (opt.graph_chunk < 0 || (opt.graph_chunk % 2) != 0)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: graph_chunk must be 0 or even and > 0");
+
+  auto *h = new ifdlbm_ctx();
+  h->alloc = g_alloc;
+  h->free_fn = g_free;
+  h->alloc_ctx = g_alloc_ctx;
+  for (int k = 0; k < ncav; ++k) {
+    int rc = validate(h, k, cavs[k]);
+    if (rc) {
+      g_create_error = h->err;
+      delete h;
+      return rc;
+    }
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) {
+    delete h;
+    return fail(nullptr, IFDLBM_ERR_CUDA, "no CUDA device is available");
+  }
+  cudaGetDevice(&h->device);
+  h->ncav = ncav;
+  h->opt = opt;
+  h->precision = opt.precision;
+  // The fused kernel is not built yet: every request runs the staged kernels.
+  h->kernel = IFDLBM_KERNEL_STAGED;
+  h->stream = (cudaStream_t)stream;
+  if (h->stream == nullptr) h->opt.graph_chunk = 0;  // the legacy stream cannot be captured
+  h->spec.assign(cavs, cavs + ncav);
+
+  const size_t tsize = opt.precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
+  int64_t off = 0, goff = 0;
+  int tile0 = 0;
+  h->cav.resize(ncav);
+  h->courant.resize(ncav);
+  std::vector<double> xix, xeH, xxi, xeta;
+  for (int k = 0; k < ncav; ++k) {
+    const ifdlbm_cavity &s = cavs[k];
+    CavDev &cv = h->cav[k];
+    cv.nx = s.nx;
+    cv.ny = s.ny;
+    cv.pitch = (s.nx + 31) / 32 * 32;
+    cv.plane = int64_t(s.ny) * cv.pitch;
+    cv.off = off;
+    off += cv.plane;
+    cv.tiles_x = (s.nx + ifd::TILE_X - 1) / ifd::TILE_X;
+    cv.tiles_y = (s.ny + ifd::TILE_Y - 1) / ifd::TILE_Y;
+    cv.tile0 = tile0;
+    tile0 += cv.tiles_x * cv.tiles_y;
+    cv.part0 = cv.tile0;
+    cv.nparts = cv.tiles_x * cv.tiles_y;
+    cv.goff = goff;
+    const int glen = std::max(s.nx, s.ny);
+    goff += glen;
+    const double L = s.geom.L, H = s.geom.H, ct = cot_deg(s.geom.theta_deg);
+    cv.c = opt.c;
+    cv.cs2 = opt.c * opt.c / 3.0;
+    cv.inv_cs2 = 1.0 / cv.cs2;
+    cv.K = std::pow(s.U_lid, 2.0 - s.n) * std::pow(H, s.n) / s.Re;  // Eq. (2.15.1)
+    cv.nm1 = s.n - 1.0;
+    cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
+    cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
+    cv.eta_b = opt.eta_b;
+    cv.dxi = 1.0 / (s.nx - 1);
+    cv.deta = 1.0 / (s.ny - 1);
+    cv.inv2dxi = 1.0 / (2.0 * cv.dxi);
+    cv.inv2deta = 1.0 / (2.0 * cv.deta);
+    cv.U = s.U_lid;
+    cv.H = H;
+    cv.rho0 = opt.rho0;
+    cv.lam0 = cv.K * std::pow(cv.gmin, cv.nm1) / cv.cs2;
+    h->max_n2 = std::max<int64_t>(h->max_n2, int64_t(s.nx) * s.ny);
+    // 1-D metric arrays of Eq. (3.8.2)
+    xix.resize(goff), xeH.resize(goff), xxi.resize(goff), xeta.resize(goff);
+    double cmax = 0;
+    for (int j = 0; j < glen; ++j) {
+      const double eta = j < s.ny ? double(j) / (s.ny - 1) : 1.0;
+      const double x_xi = L + 2.0 * H * ct * eta;
+      xxi[cv.goff + j] = x_xi;
+      xix[cv.goff + j] = 1.0 / x_xi;
+    }
+    for (int i = 0; i < glen; ++i) {
+      const double xi = i < s.nx ? double(i) / (s.nx - 1) : 1.0;
+      const double x_eta = H * ct * (2.0 * xi - 1.0);
+      xeta[cv.goff + i] = x_eta;
+      xeH[cv.goff + i] = x_eta / H;
+    }
+    for (int j = 0; j < s.ny; ++j)
+      for (int i = 0; i < s.nx; i += std::max(1, s.nx - 1))
+        for (int q = 1; q < 9; ++q) {
+          static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+          static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+          const double A = opt.c * xix[cv.goff + j];
+          const double cxi = A * (EX[q] - EY[q] * xeH[cv.goff + i]);
+          const double ceta = opt.c * EY[q] / H;
+          cmax = std::max(cmax, cv.dt * (std::fabs(cxi) / cv.dxi + std::fabs(ceta) / cv.deta));
+        }
+    h->courant[k] = cmax;
+  }
+  h->ntiles = tile0;
+  h->total_plane = off;
+  h->geo_len = goff;
+
+  auto A = [&](size_t bytes) { return dalloc(h, bytes); };
+  bool ok = true;
+  for (int p = 0; p < 2; ++p) {
+    ok &= (h->b.g[p] = A(9 * off * tsize)) != nullptr;
+    ok &= (h->b.lam[p] = (double *)A(off * sizeof(double))) != nullptr;
+  }
+  ok &= (h->b.fb = A(9 * off * tsize)) != nullptr;
+  ok &= (h->b.fp = A(9 * off * tsize)) != nullptr;
+  ok &= (h->b.fh = A(9 * off * tsize)) != nullptr;
+  ok &= (h->b.m0 = (double *)A(3 * off * sizeof(double))) != nullptr;
+  ok &= (h->b.part = (double *)A(size_t(h->ntiles) * ifd::NPART * sizeof(double))) != nullptr;
+  ok &= (h->b.resid = (double *)A(size_t(ncav) * 4 * sizeof(double))) != nullptr;
+  ok &= (h->b.tile_cav = (int *)A(size_t(h->ntiles) * sizeof(int))) != nullptr;
+  ok &= (h->b.status = (unsigned *)A(sizeof(unsigned))) != nullptr;
+  ok &= (h->b.cav = (CavDev *)A(size_t(ncav) * sizeof(CavDev))) != nullptr;
+  double *geo = (double *)A(size_t(4 * goff) * sizeof(double));
+  ok &= geo != nullptr;
+  ok &= (h->stage = (double *)A(size_t(10 * h->max_n2) * sizeof(double))) != nullptr;
+  if (!ok) {
+    release_all(h);
+    delete h;
+    return fail(nullptr, IFDLBM_ERR_OOM, "device allocation failed");
+  }
+  h->b.geo.xix = geo;
+  h->b.geo.xeH = geo + goff;
+  h->b.geo.xxi = geo + 2 * goff;
+  h->b.geo.xeta = geo + 3 * goff;
+
+  std::vector<int> tile_cav(h->ntiles);
+  for (int k = 0; k < ncav; ++k)
+    for (int t = 0; t < h->cav[k].nparts; ++t) tile_cav[h->cav[k].tile0 + t] = k;
+  std::vector<double> geo_h(4 * goff);
+  std::copy(xix.begin(), xix.end(), geo_h.begin());
+  std::copy(xeH.begin(), xeH.end(), geo_h.begin() + goff);
+  std::copy(xxi.begin(), xxi.end(), geo_h.begin() + 2 * goff);
+  std::copy(xeta.begin(), xeta.end(), geo_h.begin() + 3 * goff);
+
+  cudaStream_t s = h->stream;
+  h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
+                         geo_h.size() * sizeof(double));
+  e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
+                      cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.cav, h->cav.data(), h->cav.size() * sizeof(CavDev),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(geo, geo_h.data(), geo_h.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  // every buffer starts zeroed so that no read can ever see uninitialised memory
+  for (void *ptr : {h->b.fb, h->b.fp, h->b.fh, h->b.g[1]})
+    if (e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, 9 * off * tsize, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.m0, 0, 3 * off * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.g[0], 0, 9 * off * tsize, s);
+  if (e == cudaSuccess) {
+    if (h->precision == IFDLBM_FP64)
+      ifd::launch_init<double>(h->b.cav, h->b.tile_cav, h->b.g[0], h->b.lam[0], h->ntiles, s);
+    else
+      ifd::launch_init<float>(h->b.cav, h->b.tile_cav, h->b.g[0], h->b.lam[0], h->ntiles, s);
+    g_launches += 1;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    std::string msg = std::string("create: ") + cudaGetErrorString(e);
+    release_all(h);
+    delete h;
+    return fail(nullptr, IFDLBM_ERR_CUDA, msg);
+  }
+  *out = h;
+  return IFDLBM_OK;
+}
+
+int ifdlbm_create(int nx, int ny, ifdlbm_geometry g, double Re, double n, double U_lid,
+                  const ifdlbm_options *opt, void *stream, ifdlbm_handle *out) {
+  ifdlbm_cavity c;
+  c.nx = nx;
+  c.ny = ny;
+  c.geom = g;
+  c.Re = Re;
+  c.n = n;
+  c.U_lid = U_lid;
+  return ifdlbm_create_batch(1, &c, opt, stream, out);
+}
+
+int ifdlbm_step(ifdlbm_handle h, int nsteps) {
+  if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");
+  if (nsteps < 0) return fail(h, IFDLBM_ERR_INVALID_ARG, "nsteps must be >= 0");
+  if (nsteps == 0) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  int remaining = nsteps - 1;  // the last step also forms the residual
+  const int chunk = h->profiling ? 0 : h->opt.graph_chunk;
+  if (chunk > 0) {
+    while (remaining >= chunk) {
+      int rc = ensure_graph(h, h->cur);
+      if (rc) return rc;
+      cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
+      g_launches += int64_t(chunk) * launches_per_step(false);
+      remaining -= chunk;
+      h->steps += chunk;
+    }
+  }
+  for (; remaining > 0; --remaining) {
+    enqueue_step_any(h, h->cur, false);
+    g_launches += launches_per_step(false);
+    h->cur ^= 1;
+    h->steps += 1;
+  }
+  enqueue_step_any(h, h->cur, true);
+  g_launches += launches_per_step(true);
+  h->cur ^= 1;
+  h->steps += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "step launch");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_macros_dev(ifdlbm_handle h, int cavity, double *rho, double *u, double *v,
+                      double *psi) {
+  if (!cavity_ok(h, cavity)) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or cavity index");
+  cudaSetDevice(h->device);
+  const ifdlbm_cavity &s = h->spec[cavity];
+  if (h->precision == IFDLBM_FP64)
+    ifd::launch_macros<double>(h->b.cav, h->b.geo, cavity, h->b.g[h->cur], rho, u, v, psi, s.nx,
+                               s.ny, h->stream);
+  else
+    ifd::launch_macros<float>(h->b.cav, h->b.geo, cavity, h->b.g[h->cur], rho, u, v, psi, s.nx,
+                              s.ny, h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "macros launch");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_batch_macros(ifdlbm_handle h, int cavity, double *rho, double *u, double *v,
+                        double *psi) {
+  if (!cavity_ok(h, cavity)) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or cavity index");
+  const ifdlbm_cavity &s = h->spec[cavity];
+  const int64_t n2 = int64_t(s.nx) * s.ny;
+  double *d[4] = {h->stage, h->stage + n2, h->stage + 2 * n2, h->stage + 3 * n2};
+  double *dst[4] = {rho, u, v, psi};
+  int rc = ifdlbm_macros_dev(h, cavity, d[0], d[1], d[2], d[3]);
+  if (rc) return rc;
+  for (int k = 0; k < 4; ++k)
+    if (dst[k]) {
+      cudaError_t e = cudaMemcpyAsync(dst[k], d[k], n2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                      h->stream);
+      if (e != cudaSuccess) return cuda_fail(h, e, "macros copy");
+    }
+  return check_status(h);
+}
+
+int ifdlbm_macros(ifdlbm_handle h, double *rho, double *u, double *v, double *psi) {
+  return ifdlbm_batch_macros(h, 0, rho, u, v, psi);
+}
+
+int ifdlbm_batch_residual(ifdlbm_handle h, double *out) {
+  if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaMemcpyAsync(out, h->b.resid, size_t(h->ncav) * 4 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "residual copy");
+  return check_status(h);
+}
+
+int ifdlbm_residual(ifdlbm_handle h, double *out) {
+  if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
+  if (h->ncav == 1) return ifdlbm_batch_residual(h, out);
+  std::vector<double> all(4 * size_t(h->ncav));
+  int rc = ifdlbm_batch_residual(h, all.data());
+  std::copy(all.begin(), all.begin() + 4, out);
+  return rc;
+}
+
+int ifdlbm_get_state(ifdlbm_handle h, int cavity, double *fhat, double *lambda_prev) {
+  if (!cavity_ok(h, cavity)) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or cavity index");
+  cudaSetDevice(h->device);
+  const ifdlbm_cavity &s = h->spec[cavity];
+  const int64_t n2 = int64_t(s.nx) * s.ny;
+  if (h->precision == IFDLBM_FP64)
+    ifd::launch_export<double>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+                               h->stage + 9 * n2, s.nx, s.ny, h->stream);
+  else
+    ifd::launch_export<float>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+                              h->stage + 9 * n2, s.nx, s.ny, h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && fhat)
+    e = cudaMemcpyAsync(fhat, h->stage, 9 * n2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && lambda_prev)
+    e = cudaMemcpyAsync(lambda_prev, h->stage + 9 * n2, n2 * sizeof(double),
+                        cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_state");
+  return check_status(h);
+}
+
+int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const double *lambda_prev) {
+  if (!cavity_ok(h, cavity) || !fhat || !lambda_prev)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle, cavity index or NULL array");
+  cudaSetDevice(h->device);
+  const ifdlbm_cavity &s = h->spec[cavity];
+  const int64_t n2 = int64_t(s.nx) * s.ny;
+  cudaError_t e =
+      cudaMemcpyAsync(h->stage, fhat, 9 * n2 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->stage + 9 * n2, lambda_prev, n2 * sizeof(double),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state copy");
+  if (h->precision == IFDLBM_FP64)
+    ifd::launch_import<double>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+                               h->stage + 9 * n2, s.nx, s.ny, h->stream);
+  else
+    ifd::launch_import<float>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+                              h->stage + 9 * n2, s.nx, s.ny, h->stream);
+  g_launches += 1;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+  return IFDLBM_OK;
+}
+
+int64_t ifdlbm_state_bytes(ifdlbm_handle h) {
+  if (!h) return -1;
+  const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
+  return int64_t(9 * h->total_plane * tsize + h->total_plane * sizeof(double));
+}
+
+int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst) {
+  if (!h || !dst) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or dst");
+  cudaSetDevice(h->device);
+  const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t gb = 9 * h->total_plane * tsize;
+  cudaError_t e = cudaMemcpyAsync(dst, h->b.g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char *)dst + gb, h->b.lam[h->cur], h->total_plane * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "save_state_dev");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_load_state_dev(ifdlbm_handle h, const void *src) {
+  if (!h || !src) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or src");
+  cudaSetDevice(h->device);
+  const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t gb = 9 * h->total_plane * tsize;
+  cudaError_t e = cudaMemcpyAsync(h->b.g[h->cur], src, gb, cudaMemcpyDeviceToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.lam[h->cur], (const char *)src + gb, h->total_plane * sizeof(double),
+                        cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "load_state_dev");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_info(ifdlbm_handle h, int cavity, ifdlbm_info_t *info) {
+  if (!cavity_ok(h, cavity) || !info) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  const CavDev &cv = h->cav[cavity];
+  info->nx = cv.nx;
+  info->ny = cv.ny;
+  info->precision = h->precision;
+  info->kernel = h->kernel;
+  info->dt = cv.dt;
+  info->K = cv.K;
+  info->gamma_min = cv.gmin;
+  info->eta_b = cv.eta_b;
+  info->courant_max = h->courant[cavity];
+  info->steps = h->steps;
+  info->device_bytes = h->bytes;
+  info->h2d_bytes = h->h2d_bytes;
+  return IFDLBM_OK;
+}
+
+int ifdlbm_sync(ifdlbm_handle h) {
+  if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");
+  cudaSetDevice(h->device);
+  return check_status(h);
+}
+
+int ifdlbm_destroy(ifdlbm_handle h) {
+  if (!h) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  release_all(h);
+  delete h;
+  return IFDLBM_OK;
+}
+
+const char *ifdlbm_last_error(ifdlbm_handle h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+int64_t ifdlbm_launch_count(void) { return g_launches.load(); }
+
+int ifdlbm_profile(ifdlbm_handle h, int enable) {
+  if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  h->ev_marks.clear();
+  return IFDLBM_OK;
+}
+
+int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *launches) {
+  if (!h || kernel < 0 || kernel >= IFDLBM_KPROF_COUNT || !total_ms || !launches)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "profile sync");
+  double tot = 0;
+  int64_t n = 0;
+  for (auto &m : h->ev_marks)
+    if (m.first == kernel) {
+      float ms = 0;
+      e = cudaEventElapsedTime(&ms, h->ev_pool[m.second.first], h->ev_pool[m.second.second]);
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
+      tot += ms;
+      ++n;
+    }
+  *total_ms = tot;
+  *launches = n;
+  return IFDLBM_OK;
+}
+
+}  // extern "C"

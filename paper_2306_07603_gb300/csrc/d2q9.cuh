@@ -1,0 +1,109 @@
+// Device-side lattice arithmetic of the IFDLBM step (D2Q9).
+//
+// All distributions are handled as deviations from the rest equilibrium,
+// g_i = F_i - w_i rho0 (F = f, f-hat, f-bar, ...). Every transform of the
+// scheme is affine with coefficients summing to one and every difference
+// of a constant vanishes, so the scheme acts on g exactly as on F; only
+// the moments (Eqs. 2.10-2.11) and the equilibrium (Eq. 2.8) drop their
+// rho0 terms.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace ifd {
+
+// D2Q9 velocity directions, Eq. (2.9): e_0 = 0, e_1..4 axes, e_5..8 diagonals.
+__host__ __device__ constexpr int ex(int i) {
+  return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int i) {
+  return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+// Weights w_i and pressure weights wbar_i of Eq. (2.9).
+__host__ __device__ constexpr double wgt(int i) {
+  return i == 0 ? 4.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+__host__ __device__ constexpr double wbar(int i) {
+  return i == 0 ? -5.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Velocity and pressure of a deviation set, Eqs. (2.10)-(2.11):
+//   u = c sum_i e_i g_i,
+//   P = c_s^2 / wbar_0 (-sum_{i>0} g_i + w_0 |u|^2 / (2 c_s^2)).
+template <class T>
+__device__ __forceinline__ void moments(const T g[9], T c, T cs2, T &ux, T &uy, T &P) {
+  ux = c * ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]));
+  uy = c * ((g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]));
+  T s = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
+  T uu = ux * ux + uy * uy;
+  P = (cs2 / T(wbar(0))) * (-s + T(wgt(0)) * uu / (T(2) * cs2));
+}
+
+// Designed equilibrium, Eq. (2.8) (quadratic term over 2 c_s^4), minus w_i rho0.
+template <class T>
+__device__ __forceinline__ void equilibrium(T P, T ux, T uy, T c, T inv_cs2, T geq[9]) {
+  const T uu = ux * ux + uy * uy;
+  const T pterm = P * inv_cs2;
+  const T half_inv_cs2 = T(0.5) * inv_cs2;
+  const T half_inv_cs4 = half_inv_cs2 * inv_cs2;
+  const T base = -uu * half_inv_cs2;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const T cu = c * (T(ex(i)) * ux + T(ey(i)) * uy);
+    geq[i] = T(wbar(i)) * pterm + T(wgt(i)) * (cu * inv_cs2 + cu * cu * half_inv_cs4 + base);
+  }
+}
+
+// Relaxation time of Step (2): strain rate from f^ne (Eqs. 2.12-2.13, with
+// f = f(f-hat, lam_prev) of Eq. 2.18), |gamma-dot| = sqrt(2 D:D), the
+// clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) (Eq. 1.4) and
+// lam = mu / c_s^2 (Eq. 2.14). Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i).
+// Always FP64.
+__device__ __forceinline__ double relaxation_time(double Pxx, double Pxy, double Pyy,
+                                                  double lam_prev, const CavDev &cv) {
+  // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
+  const double k = -2.0 / ((2.0 * lam_prev + cv.dt) * cv.cs2);
+  const double Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;
+  double gd = sqrt(0.5 * (Sxx * Sxx + 2.0 * Sxy * Sxy + Syy * Syy));
+  gd = gd > cv.gmin ? gd : cv.gmin;
+  return cv.K * pow(gd, cv.nm1) * cv.inv_cs2;
+}
+
+// Second moments of the non-equilibrium deviation d_i = g_i - geq_i.
+template <class T>
+__device__ __forceinline__ void second_moments(const T d[9], T c, T &Pxx, T &Pxy, T &Pyy) {
+  const T c2 = c * c;
+  const T diag = (d[5] + d[6]) + (d[7] + d[8]);
+  Pxx = c2 * ((d[1] + d[3]) + diag);
+  Pyy = c2 * ((d[2] + d[4]) + diag);
+  Pxy = c2 * ((d[5] - d[6]) + (d[7] - d[8]));
+}
+
+// Mixed difference of Eqs. (2.5)-(2.7) times 2 d:
+//   eta_b (F[k+1] - F[k-1]) + (1 - eta_b) U,
+// U the 2nd-order upwind difference times 2 d on the side given by the
+// sign of the contravariant velocity (c >= 0 uses k-2..k, c < 0 uses
+// k..k+2), reduced to first order where that stencil would leave the grid
+// (k = 1 for c >= 0, k = N-2 for c < 0).
+template <class T>
+__device__ __forceinline__ T dmix2(T fm2, T fm1, T f0, T fp1, T fp2, bool pos, bool lo, bool hi,
+                                   T eta_b) {
+  const T central = fp1 - fm1;
+  T up;
+  if (pos)
+    up = lo ? T(2) * (f0 - fm1) : (T(3) * f0 - T(4) * fm1 + fm2);
+  else
+    up = hi ? T(2) * (fp1 - f0) : -(T(3) * f0 - T(4) * fp1 + fp2);
+  return eta_b * central + (T(1) - eta_b) * up;
+}
+
+// Contravariant velocities of Eq. (3.4) for the trapezoid map, where
+// eta_x = 0, eta_y = 1/H, xi_x = 1/x_xi, xi_y = -x_eta/(H x_xi):
+//   c_{i xi} = c xi_x (e_ix - e_iy x_eta/H),  c_{i eta} = c e_iy / H.
+__device__ __forceinline__ double cxi_of(int q, double A, double B) {
+  // A = c xi_x, B = c xi_x x_eta / H
+  return double(ex(q)) * A - double(ey(q)) * B;
+}
+
+}  // namespace ifd

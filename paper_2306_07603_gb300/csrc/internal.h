@@ -1,0 +1,92 @@
+// Internal structures shared by the host API (capi.cu) and the kernels.
+// Not part of the public ABI (include/ifdlbm.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ifd {
+
+// Per-cavity constants, resident in device global memory (one entry per
+// cavity of a handle). Offsets are in elements of the arena they index.
+struct CavDev {
+  int nx, ny, pitch;        // nodes along xi / eta; row pitch in elements
+  int tile0, tiles_x, tiles_y;  // staged-kernel tiles of this cavity
+  int64_t plane;            // ny * pitch
+  int64_t off;              // start of plane 0 of this cavity (per-plane units)
+  int64_t goff;             // start of this cavity's 1-D metric arrays
+  int part0;                // first residual-partial slot of this cavity
+  int nparts;               // number of partial slots
+  double dt, K, nm1, gmin;  // time step, consistency coeff., n - 1, shear clamp
+  double eta_b;             // blend of Eq. (2.5)
+  double c, cs2, inv_cs2;   // lattice speed, c_s^2, 1/c_s^2
+  double dxi, deta;         // computational grid spacings
+  double inv2dxi, inv2deta; // 1/(2 dxi), 1/(2 deta)
+  double U, H, rho0;        // lid speed, height, reference density
+  double lam0;              // Eq. (2.14) at zero shear (initial lambda_prev)
+};
+
+// 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
+//   xix[j]  = xi_x(eta_j) = 1 / x_xi(eta_j)             (ny entries)
+//   xeH[i]  = x_eta(xi_i) / H                           (nx entries)
+//   xxi[j]  = x_xi(eta_j)    (Jacobian J = x_xi * H)    (ny entries)
+//   xeta[i] = x_eta(xi_i)    (stream function)          (nx entries)
+struct Geo {
+  const double *xix, *xeH, *xxi, *xeta;
+};
+
+// Device buffers of a handle. T is double (FP64) or float (FP32DEV).
+struct Bufs {
+  void *g[2];        // 9 planes per cavity: f-hat deviation g_i, ping-pong
+  double *lam[2];    // 1 plane per cavity: relaxation time, ping-pong
+  void *fb;          // 9 planes: f-bar^+ (staged kernels)
+  void *fp;          // 9 planes: f-hat^+ (staged kernels)
+  void *fh;          // 9 planes: f(t + dt/2) (staged kernels)
+  double *m0;        // 3 planes: u, v, P at the start of the step
+  double *part;      // residual partials [nparts_total][8]
+  double *resid;     // [ncav][4] residual outputs
+  int *tile_cav;     // staged tile -> cavity
+  unsigned *status;  // bit 0: non-finite velocity seen
+  CavDev *cav;       // [ncav]
+  Geo geo;
+};
+
+struct StepArgs {
+  const CavDev *cav;
+  Geo geo;
+  const int *tile_cav;
+  const void *g_in;
+  void *g_out;
+  const double *lam_in;
+  double *lam_out;
+  void *fb, *fp, *fh;
+  double *m0;
+  double *part;
+  unsigned *status;
+  int want_residual;
+};
+
+// Staged kernels (staged.cu)
+template <class T> void launch_collide(const StepArgs &a, int ntiles, cudaStream_t s);
+template <class T> void launch_half(const StepArgs &a, int ntiles, cudaStream_t s);
+template <class T> void launch_full(const StepArgs &a, int ntiles, cudaStream_t s);
+void launch_residual_reduce(const CavDev *cav, const double *part, double *resid, int ncav,
+                            cudaStream_t s);
+
+// Utility kernels (staged.cu)
+template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,
+                                    int ntiles, cudaStream_t s);
+template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const void *g,
+                                      double *rho, double *u, double *v, double *psi,
+                                      int nx, int ny, cudaStream_t s);
+template <class T> void launch_export(const CavDev *cav, int cavity, const void *g,
+                                      const double *lam, double *fhat, double *lamo, int nx,
+                                      int ny, cudaStream_t s);
+template <class T> void launch_import(const CavDev *cav, int cavity, void *g, double *lam,
+                                      const double *fhat, const double *lami, int nx, int ny,
+                                      cudaStream_t s);
+
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 8;
+constexpr int NPART = 8;  // doubles per residual partial slot
+
+}  // namespace ifd

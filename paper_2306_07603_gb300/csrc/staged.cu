@@ -1,0 +1,438 @@
+// Staged IFDLBM step: three launches per time step, no recomputation.
+//
+//   k_collide  every node: Step (2) (moments, f^eq, lagged power-law lam),
+//              Step (3) f-hat^+ (Eq. 2.15) and f-bar^+ (Eq. 2.16)
+//   k_half     every node: Step (4) half step f-bar(t+dt/2) (Eq. 3.7), its
+//              moments and f(t+dt/2) (Eq. 2.17); wall nodes by
+//              non-equilibrium extrapolation from their inner neighbour
+//   k_full     every node: Step (5) f-hat(t+dt) (Eq. 3.6); wall nodes by
+//              non-equilibrium extrapolation (Step 6); residual partials of
+//              Eq. (2.19) and Eq. (5.1)
+//
+// On GB300 the FP64 pipe runs at a small fraction of the FP32 rate, so the
+// FP64 step is bound by FP64 instructions, not bytes: this organisation
+// keeps every node's arithmetic to exactly one evaluation and pays with
+// intermediate planes (f-bar^+, f-hat^+, f(t+dt/2)) that stay in L2 for
+// the grid sizes of a cavity sweep.
+//
+// A wall node (i, j) takes its neighbour (clamp(i, 1, nx-2), clamp(j, 1,
+// ny-2)): the adjacent node along the grid normal on a side, the diagonal
+// node at a corner. The lid nodes 0 < i < nx-1 of row ny-1 move at (U, 0);
+// every other wall node, the two top corners included, is at rest.
+#include <cstdint>
+
+#include "d2q9.cuh"
+#include "internal.h"
+
+namespace ifd {
+
+struct NodeRef {
+  int cav, i, j;
+  bool valid;
+};
+
+__device__ __forceinline__ NodeRef tile_node(const int *tile_cav, const CavDev *cavs) {
+  NodeRef r;
+  const int t = blockIdx.x;
+  r.cav = tile_cav[t];
+  const CavDev &cv = cavs[r.cav];
+  const int lt = t - cv.tile0;
+  r.i = (lt % cv.tiles_x) * TILE_X + threadIdx.x;
+  r.j = (lt / cv.tiles_x) * TILE_Y + threadIdx.y;
+  r.valid = r.i < cv.nx && r.j < cv.ny;
+  return r;
+}
+
+template <class T>
+__device__ __forceinline__ void load9(const T *base, int64_t plane, int64_t node, T v[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) v[q] = base[q * plane + node];
+}
+
+template <class T>
+__device__ __forceinline__ void store9(T *base, int64_t plane, int64_t node, const T v[9]) {
+#pragma unroll
+  for (int q = 0; q < 9; ++q) base[q * plane + node] = v[q];
+}
+
+// ---------------------------------------------------------------------------
+// Step (2)-(3): collision-side transforms, pointwise
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_collide(StepArgs a) {
+  const NodeRef r = tile_node(a.tile_cav, a.cav);
+  if (!r.valid) return;
+  const CavDev &cv = a.cav[r.cav];
+  const int64_t node = int64_t(r.j) * cv.pitch + r.i;
+  const int64_t b9 = 9 * cv.off;
+  T g[9];
+  load9((const T *)a.g_in + b9, cv.plane, node, g);
+  const double lam_prev = a.lam_in[cv.off + node];
+
+  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
+  T ux, uy, P;
+  moments(g, c, cs2, ux, uy, P);                 // Eqs. (2.10)-(2.11)
+  T geq[9];
+  equilibrium(P, ux, uy, c, ics2, geq);          // Eq. (2.8)
+  T d[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) d[q] = g[q] - geq[q];
+  T pxx, pxy, pyy;
+  second_moments(d, c, pxx, pxy, pyy);
+  const double lam = relaxation_time(double(pxx), double(pxy), double(pyy), lam_prev, cv);
+  a.lam_out[cv.off + node] = lam;                // lam(t), also next lam_prev
+
+  const T L = T(lam), dt = T(cv.dt);
+  const T i2 = T(1) / (T(2) * L + dt);
+  const T ap = (T(2) * L - dt) * i2, bp = T(2) * dt * i2;     // Eq. (2.15)
+  const T i4 = T(1) / (T(4) * L + T(2) * dt);
+  const T ab = (T(4) * L - dt) * i4, bb = T(3) * dt * i4;     // Eq. (2.16)
+  T *fp = (T *)a.fp + b9;
+  T *fb = (T *)a.fb + b9;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    fp[q * cv.plane + node] = ap * g[q] + bp * geq[q];
+    fb[q * cv.plane + node] = ab * g[q] + bb * geq[q];
+  }
+  double *m0 = a.m0 + 3 * cv.off;
+  m0[node] = double(ux);
+  m0[cv.plane + node] = double(uy);
+  m0[2 * cv.plane + node] = double(P);
+}
+
+// Advection term (c_{q xi} D_xi + c_{q eta} D_eta) F_q at interior node
+// (i, j) of plane F (Eqs. 3.4-3.7 with the mixed scheme of Eq. 2.5).
+template <class T>
+__device__ __forceinline__ T advect(const T *F, int64_t node, int pitch, int i, int j, int nx,
+                                    int ny, T cxi, T ceta, const CavDev &cv) {
+  // clamped neighbour offsets: the clamped values are never used
+  const int im2 = i >= 2 ? -2 : -1, ip2 = i <= nx - 3 ? 2 : 1;
+  const int jm2 = j >= 2 ? -2 : -1, jp2 = j <= ny - 3 ? 2 : 1;
+  const T f0 = F[node];
+  const T eta_b = T(cv.eta_b);
+  const T dxi = dmix2(F[node + im2], F[node - 1], f0, F[node + 1], F[node + ip2], cxi >= T(0),
+                      i == 1, i == nx - 2, eta_b) * T(cv.inv2dxi);
+  const int64_t p = pitch;
+  const T deta = dmix2(F[node + jm2 * p], F[node - p], f0, F[node + p], F[node + jp2 * p],
+                       ceta >= T(0), j == 1, j == ny - 2, eta_b) * T(cv.inv2deta);
+  return cxi * dxi + ceta * deta;
+}
+
+// Wall-node rule (Sec. 4): F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
+template <class T>
+__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
+  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
+  T ux, uy, P;
+  moments(F, c, cs2, ux, uy, P);
+  T fw[9], fn[9];
+  equilibrium(P, uwx, uwy, c, ics2, fw);
+  equilibrium(P, ux, uy, c, ics2, fn);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = fw[q] + (F[q] - fn[q]);
+}
+
+__device__ __forceinline__ void wall_neighbour(const CavDev &cv, int i, int j, int &ii, int &jj,
+                                               bool &wall, double &uwx) {
+  wall = (i == 0) | (j == 0) | (i == cv.nx - 1) | (j == cv.ny - 1);
+  ii = min(max(i, 1), cv.nx - 2);
+  jj = min(max(j, 1), cv.ny - 2);
+  uwx = (j == cv.ny - 1 && i > 0 && i < cv.nx - 1) ? cv.U : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Step (4): half step and f(t + dt/2)
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
+  const NodeRef r = tile_node(a.tile_cav, a.cav);
+  if (!r.valid) return;
+  const CavDev &cv = a.cav[r.cav];
+  int ii, jj;
+  bool wall;
+  double uwx;
+  wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx);
+  const int64_t b9 = 9 * cv.off;
+  const T *fb = (const T *)a.fb + b9;
+  const int64_t node = int64_t(jj) * cv.pitch + ii;
+  const double lam = a.lam_out[cv.off + node];
+
+  const double A = cv.c * a.geo.xix[cv.goff + jj];         // c xi_x
+  const double B = A * a.geo.xeH[cv.goff + ii];            // c xi_x x_eta / H
+  const T ceta_unit = T(cv.c / cv.H);
+  const T hdt = T(0.5 * cv.dt);
+  T fbar[9];
+  fbar[0] = fb[node];
+#pragma unroll
+  for (int q = 1; q < 9; ++q) {
+    const T *F = fb + q * cv.plane;
+    const T cxi = T(cxi_of(q, A, B));
+    const T ceta = T(ey(q)) * ceta_unit;
+    fbar[q] = F[node] - hdt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, cxi, ceta, cv);
+  }
+  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
+  T ux, uy, P;
+  moments(fbar, c, cs2, ux, uy, P);              // Eqs. (2.10)-(2.11) on f-bar
+  T geq[9];
+  equilibrium(P, ux, uy, c, ics2, geq);
+  const T L = T(lam), dt = T(cv.dt);
+  const T i4 = T(1) / (T(4) * L + dt);
+  const T ah = T(4) * L * i4, bh = dt * i4;      // Eq. (2.17)
+  T fh[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) fh[q] = ah * fbar[q] + bh * geq[q];
+  if (wall) nee(fh, T(uwx), T(0), cv);
+  store9((T *)a.fh + b9, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
+}
+
+// ---------------------------------------------------------------------------
+// Steps (5)-(6): full step, wall nodes, residual partials
+// ---------------------------------------------------------------------------
+struct Partial {
+  double du2, u2, dP2, P2, ek, du2max, u2max;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block reduction of the residual partials into slot `slot` (fixed order).
+template <int NWARPS>
+__device__ __forceinline__ void block_partial(Partial p, double *part, int slot) {
+  __shared__ double sh[NWARPS][7];
+  const int lane = threadIdx.x + threadIdx.y * blockDim.x;
+  const int w = lane >> 5, l = lane & 31;
+  double v[7] = {warp_sum(p.du2), warp_sum(p.u2), warp_sum(p.dP2), warp_sum(p.P2),
+                 warp_sum(p.ek),  warp_max(p.du2max), warp_max(p.u2max)};
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sh[w][k] = v[k];
+  __syncthreads();
+  if (lane < 7) {
+    double acc = sh[0][lane];
+    for (int k = 1; k < NWARPS; ++k) acc = lane < 5 ? acc + sh[k][lane] : fmax(acc, sh[k][lane]);
+    part[int64_t(slot) * NPART + lane] = acc;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
+  const NodeRef r = tile_node(a.tile_cav, a.cav);
+  const CavDev &cv = a.cav[r.cav];
+  Partial p = {0, 0, 0, 0, 0, 0, 0};
+  if (r.valid) {
+    int ii, jj;
+    bool wall;
+    double uwx;
+    wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx);
+    const int64_t b9 = 9 * cv.off;
+    const T *fh = (const T *)a.fh + b9;
+    const T *fp = (const T *)a.fp + b9;
+    const int64_t node = int64_t(jj) * cv.pitch + ii;
+    const double A = cv.c * a.geo.xix[cv.goff + jj];
+    const double B = A * a.geo.xeH[cv.goff + ii];
+    const T ceta_unit = T(cv.c / cv.H);
+    const T dt = T(cv.dt);
+    T gn[9];
+    gn[0] = fp[node];
+#pragma unroll
+    for (int q = 1; q < 9; ++q) {
+      const T *F = fh + q * cv.plane;
+      const T cxi = T(cxi_of(q, A, B));
+      const T ceta = T(ey(q)) * ceta_unit;
+      gn[q] = fp[q * cv.plane + node] -
+              dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, cxi, ceta, cv);  // Eq. (3.6)
+    }
+    if (wall) nee(gn, T(uwx), T(0), cv);
+    const int64_t me = int64_t(r.j) * cv.pitch + r.i;
+    store9((T *)a.g_out + b9, cv.plane, me, gn);
+
+    T ux, uy, P;
+    moments(gn, T(cv.c), T(cv.cs2), ux, uy, P);
+    const double u1 = double(ux), v1 = double(uy), P1 = double(P);
+    if (!(isfinite(u1) && isfinite(v1))) atomicOr(a.status, 1u);
+    if (a.want_residual) {
+      const double *m0 = a.m0 + 3 * cv.off;
+      const double du = u1 - m0[me], dv = v1 - m0[cv.plane + me], dP = P1 - m0[2 * cv.plane + me];
+      p.du2 = du * du + dv * dv;
+      p.u2 = u1 * u1 + v1 * v1;
+      p.dP2 = dP * dP;
+      p.P2 = P1 * P1;
+      p.du2max = p.du2;
+      p.u2max = p.u2;
+      const double wx = ((r.i == 0 || r.i == cv.nx - 1) ? 0.5 : 1.0) * cv.dxi;
+      const double wy = ((r.j == 0 || r.j == cv.ny - 1) ? 0.5 : 1.0) * cv.deta;
+      p.ek = 0.5 * wx * wy * (a.geo.xxi[cv.goff + r.j] * cv.H) * p.u2;  // Eq. (5.1)
+    }
+  }
+  if (a.want_residual) block_partial<TILE_X * TILE_Y / 32>(p, a.part, blockIdx.x);
+}
+
+// One block per cavity: fixed-order reduction of that cavity's partials.
+__global__ void k_residual_reduce(const CavDev *cavs, const double *part, double *resid) {
+  const CavDev &cv = cavs[blockIdx.x];
+  __shared__ double sh[256][7];
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int s = threadIdx.x; s < cv.nparts; s += blockDim.x) {
+    const double *pp = part + int64_t(cv.part0 + s) * NPART;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += pp[k];
+    acc[5] = fmax(acc[5], pp[5]);
+    acc[6] = fmax(acc[6], pp[6]);
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) sh[threadIdx.x][k] = acc[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) sh[threadIdx.x][k] += sh[threadIdx.x + w][k];
+      sh[threadIdx.x][5] = fmax(sh[threadIdx.x][5], sh[threadIdx.x + w][5]);
+      sh[threadIdx.x][6] = fmax(sh[threadIdx.x][6], sh[threadIdx.x + w][6]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    double *o = resid + 4 * blockIdx.x;
+    o[0] = sqrt(sh[0][0]) / sqrt(sh[0][1]);   // E(u), Eq. (2.19)
+    o[1] = sqrt(sh[0][2]) / sqrt(sh[0][3]);   // E(P), Eq. (2.19)
+    o[2] = sqrt(sh[0][5]) / sqrt(sh[0][6]);   // max-norm velocity residual
+    o[3] = sh[0][4];                           // kinetic energy, Eq. (5.1)
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Initial state (Step 1), macros / stream function, state import and export
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_init(const CavDev *cavs, const int *tile_cav,
+                                                          T *g, double *lam) {
+  const NodeRef r = tile_node(tile_cav, cavs);
+  if (!r.valid) return;
+  const CavDev &cv = cavs[r.cav];
+  const int64_t node = int64_t(r.j) * cv.pitch + r.i;
+  const bool lid = r.j == cv.ny - 1 && r.i > 0 && r.i < cv.nx - 1;
+  T geq[9];
+  equilibrium(T(0), lid ? T(cv.U) : T(0), T(0), T(cv.c), T(cv.inv_cs2), geq);
+  store9(g + 9 * cv.off, cv.plane, node, geq);
+  lam[cv.off + node] = cv.lam0;
+}
+
+// One thread per xi = const line: macros at every node, then
+// psi_j = psi_{j-1} + (I_j + I_{j-1}) deta / 2 with I = u y_eta - v x_eta.
+template <class T>
+__global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const T *g, double *rho,
+                         double *u, double *v, double *psi) {
+  const CavDev &cv = cavs[cavity];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cv.nx) return;
+  const T *gb = g + 9 * cv.off;
+  const double xeta = geo.xeta[cv.goff + i];
+  double acc = 0.0, Iprev = 0.0;
+  for (int j = 0; j < cv.ny; ++j) {
+    T gg[9];
+    load9(gb, cv.plane, int64_t(j) * cv.pitch + i, gg);
+    T ux, uy, P;
+    moments(gg, T(cv.c), T(cv.cs2), ux, uy, P);
+    const int64_t o = int64_t(j) * cv.nx + i;
+    if (rho) rho[o] = cv.rho0 + double(P) * cv.inv_cs2;
+    if (u) u[o] = double(ux);
+    if (v) v[o] = double(uy);
+    const double I = double(ux) * cv.H - double(uy) * xeta;
+    if (j > 0) acc += 0.5 * (I + Iprev) * cv.deta;
+    Iprev = I;
+    if (psi) psi[o] = acc;
+  }
+}
+
+template <class T>
+__global__ void k_export(const CavDev *cavs, int cavity, const T *g, const double *lam,
+                         double *fhat, double *lamo) {
+  const CavDev &cv = cavs[cavity];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= cv.nx) return;
+  const int64_t node = int64_t(j) * cv.pitch + i, o = int64_t(j) * cv.nx + i;
+  const int64_t n2 = int64_t(cv.nx) * cv.ny;
+  if (fhat)
+#pragma unroll
+    for (int q = 0; q < 9; ++q)
+      fhat[q * n2 + o] = double(g[9 * cv.off + q * cv.plane + node]) + wgt(q) * cv.rho0;
+  if (lamo) lamo[o] = lam[cv.off + node];
+}
+
+template <class T>
+__global__ void k_import(const CavDev *cavs, int cavity, T *g, double *lam, const double *fhat,
+                         const double *lami) {
+  const CavDev &cv = cavs[cavity];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+  if (i >= cv.nx) return;
+  const int64_t node = int64_t(j) * cv.pitch + i, o = int64_t(j) * cv.nx + i;
+  const int64_t n2 = int64_t(cv.nx) * cv.ny;
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    g[9 * cv.off + q * cv.plane + node] = T(fhat[q * n2 + o] - wgt(q) * cv.rho0);
+  lam[cv.off + node] = lami[o];
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+static const dim3 kTile(TILE_X, TILE_Y);
+
+template <class T> void launch_collide(const StepArgs &a, int ntiles, cudaStream_t s) {
+  k_collide<T><<<ntiles, kTile, 0, s>>>(a);
+}
+template <class T> void launch_half(const StepArgs &a, int ntiles, cudaStream_t s) {
+  k_half<T><<<ntiles, kTile, 0, s>>>(a);
+}
+template <class T> void launch_full(const StepArgs &a, int ntiles, cudaStream_t s) {
+  k_full<T><<<ntiles, kTile, 0, s>>>(a);
+}
+void launch_residual_reduce(const CavDev *cav, const double *part, double *resid, int ncav,
+                            cudaStream_t s) {
+  k_residual_reduce<<<ncav, 256, 0, s>>>(cav, part, resid);
+}
+template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,
+                                    int ntiles, cudaStream_t s) {
+  k_init<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (T *)g, lam);
+}
+template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const void *g,
+                                      double *rho, double *u, double *v, double *psi, int nx,
+                                      int ny, cudaStream_t s) {
+  (void)ny;
+  k_macros<T><<<(nx + 127) / 128, 128, 0, s>>>(cav, geo, cavity, (const T *)g, rho, u, v, psi);
+}
+template <class T> void launch_export(const CavDev *cav, int cavity, const void *g,
+                                      const double *lam, double *fhat, double *lamo, int nx,
+                                      int ny, cudaStream_t s) {
+  k_export<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, (const T *)g, lam, fhat,
+                                                          lamo);
+}
+template <class T> void launch_import(const CavDev *cav, int cavity, void *g, double *lam,
+                                      const double *fhat, const double *lami, int nx, int ny,
+                                      cudaStream_t s) {
+  k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, (T *)g, lam, fhat, lami);
+}
+
+#define IFD_INSTANTIATE(T)                                                                     \
+  template void launch_collide<T>(const StepArgs &, int, cudaStream_t);                       \
+  template void launch_half<T>(const StepArgs &, int, cudaStream_t);                          \
+  template void launch_full<T>(const StepArgs &, int, cudaStream_t);                          \
+  template void launch_init<T>(const CavDev *, const int *, void *, double *, int,            \
+                               cudaStream_t);                                                  \
+  template void launch_macros<T>(const CavDev *, Geo, int, const void *, double *, double *,  \
+                                 double *, double *, int, int, cudaStream_t);                 \
+  template void launch_export<T>(const CavDev *, int, const void *, const double *, double *, \
+                                 double *, int, int, cudaStream_t);                           \
+  template void launch_import<T>(const CavDev *, int, void *, double *, const double *,       \
+                                 const double *, int, int, cudaStream_t);
+IFD_INSTANTIATE(double)
+IFD_INSTANTIATE(float)
+
+}  // namespace ifd

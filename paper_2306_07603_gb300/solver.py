@@ -1,0 +1,94 @@
+"""Convenience wrapper owning one library handle (one cavity or a batch).
+
+It only marshals arguments to the C ABI (``capi``); every step of the
+method runs in libifdlbm.so on the GPU. The handle gets its own CUDA stream
+from PyTorch and allocates through PyTorch's caching allocator.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import capi
+
+_PREC = {"fp64": capi.IFDLBM_FP64, "fp32dev": capi.IFDLBM_FP32DEV}
+_KERN = {"auto": capi.IFDLBM_KERNEL_AUTO, "staged": capi.IFDLBM_KERNEL_STAGED,
+         "fused": capi.IFDLBM_KERNEL_FUSED}
+
+
+def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, dt=None,
+                 gamma_min=None, graph_chunk=None):
+    opt = capi.ifdlbm_default_options()
+    opt.precision = _PREC[precision]
+    opt.kernel = _KERN[kernel]
+    for name, val in (("eta_b", eta_b), ("cfl", cfl), ("c", c), ("dt", dt),
+                      ("gamma_min", gamma_min), ("graph_chunk", graph_chunk)):
+        if val is not None:
+            setattr(opt, name, val)
+    return opt
+
+
+def cavity(nx, ny, Re, n, theta_deg=60.0, U_lid=0.1, L=1.0, H=1.0):
+    """A cavity description (ifdlbm_cavity)."""
+    return capi.ifdlbm_cavity(int(nx), int(ny), capi.ifdlbm_geometry(L, H, theta_deg),
+                              float(Re), float(n), float(U_lid))
+
+
+class Solver:
+    def __init__(self, cavities, stream=None, **options):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required: the IFDLBM library has no CPU path")
+        capi.load_library()
+        capi.use_torch_allocator()
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        self.cavities = list(cavities)
+        self.opt = make_options(**options)
+        self.h = capi.ifdlbm_create_batch(self.cavities, self.opt, self.stream.cuda_stream)
+
+    @property
+    def ncav(self):
+        return len(self.cavities)
+
+    def step(self, nsteps=1):
+        capi.ifdlbm_step(self.h, nsteps)
+        return self
+
+    def residual(self):
+        out = np.zeros((self.ncav, 4))
+        capi.ifdlbm_batch_residual(self.h, out)
+        return out
+
+    def macros(self, cavity=0):
+        c = self.cavities[cavity]
+        f = {k: np.zeros((c.ny, c.nx)) for k in ("rho", "u", "v", "psi")}
+        capi.ifdlbm_batch_macros(self.h, cavity, f["rho"], f["u"], f["v"], f["psi"])
+        return f
+
+    def get_state(self, cavity=0):
+        c = self.cavities[cavity]
+        fhat = np.zeros((9, c.ny, c.nx))
+        lam = np.zeros((c.ny, c.nx))
+        capi.ifdlbm_get_state(self.h, cavity, fhat, lam)
+        return fhat, lam
+
+    def set_state(self, cavity, fhat, lam):
+        capi.ifdlbm_set_state(self.h, cavity, np.ascontiguousarray(fhat, dtype=np.float64),
+                              np.ascontiguousarray(lam, dtype=np.float64))
+
+    def info(self, cavity=0):
+        return capi.ifdlbm_info(self.h, cavity)
+
+    def sync(self):
+        capi.ifdlbm_sync(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            capi.ifdlbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,94 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+entry point include/ifdlbm.h declares; argument validation happens before
+any device work (no compute calls are made here)."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ifdlbm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_07603_gb300 import capi
+    if not os.path.exists(capi.LIB_PATH):
+        if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+            pytest.skip("nvcc not available to build libifdlbm.so")
+        from paper_2306_07603_gb300 import build
+        build.build()
+    return capi.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ifdlbm_\w+)\s*\(", text)) - {"ifdlbm_alloc_fn", "ifdlbm_free_fn"})
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2306_07603_gb300 import capi
+    assert set(declared_functions()) <= set(capi._SIGS)
+
+
+def test_default_options(lib):
+    from paper_2306_07603_gb300 import capi
+    o = capi.ifdlbm_default_options()
+    assert (o.cfl, o.c, o.eta_b, o.rho0) == (0.5, 1.0, 0.5, 1.0)
+    assert o.precision == capi.IFDLBM_FP64 and o.graph_chunk == 32
+
+
+@pytest.mark.parametrize("args,frag", [
+    ((4, 9, (1, 1, 60), 100, 0.75, 0.1), ">= 5"),
+    ((9, 9, (1, 1, 0), 100, 0.75, 0.1), "theta"),
+    ((9, 9, (1, 1, 91), 100, 0.75, 0.1), "theta"),
+    ((9, 9, (0, 1, 60), 100, 0.75, 0.1), "L and H"),
+    ((9, 9, (1, 1, 60), -1, 0.75, 0.1), "Re, n"),
+    ((9, 9, (1, 1, 60), 100, 0.0, 0.1), "Re, n"),
+    ((9, 9, (1, 1, 60), 100, 0.75, 0.0), "Re, n"),
+])
+def test_invalid_arguments_rejected_before_device_use(lib, args, frag):
+    from paper_2306_07603_gb300 import capi
+    with pytest.raises(capi.IfdlbmError) as e:
+        capi.ifdlbm_create(*args)
+    assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG
+    assert frag in str(e.value)
+
+
+def test_invalid_options_rejected(lib):
+    from paper_2306_07603_gb300 import capi
+    for field, val in (("eta_b", 1.5), ("cfl", 0.0), ("precision", 7), ("graph_chunk", 3)):
+        o = capi.ifdlbm_default_options()
+        setattr(o, field, val)
+        with pytest.raises(capi.IfdlbmError) as e:
+            capi.ifdlbm_create(9, 9, (1, 1, 60), 100, 0.75, 0.1, o)
+        assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback_without_a_gpu(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2306_07603_gb300 import capi
+    with pytest.raises(capi.IfdlbmError) as e:
+        capi.ifdlbm_create(9, 9, (1, 1, 60), 100, 0.75, 0.1)
+    assert e.value.code == capi.IFDLBM_ERR_CUDA
+
+
+def test_null_handle_calls_fail_cleanly(lib):
+    from paper_2306_07603_gb300 import capi
+    assert lib.ifdlbm_step(None, 1) == capi.IFDLBM_ERR_INVALID_ARG
+    assert lib.ifdlbm_sync(None) == capi.IFDLBM_ERR_INVALID_ARG
+    assert lib.ifdlbm_destroy(None) == capi.IFDLBM_OK
+    assert lib.ifdlbm_state_bytes(None) == -1
