@@ -226,6 +226,40 @@ const char *ifdlbm_last_error(ifdlbm_handle h);
 int ifdlbm_profile(ifdlbm_handle h, int enable);
 int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *launches);
 
+/* Residuals between two sets of macroscopic fields, for callers that may
+ * not allocate device memory. The paper has no counterpart: this is a
+ * service of the library, not a step of the method.
+ *
+ * Some callers cannot call cudaMalloc: code that runs inside another
+ * framework's stream-ordered memory pool or a fixed device-memory budget
+ * (a multi-tenant service, a real-time loop), where an allocation would
+ * synchronise the device, fragment the pool or fail at the worst moment.
+ * This entry point allocates nothing, directly or through any library
+ * (PyTorch's allocator included). Its scratch, one partial sum per 256
+ * nodes, is a fixed 512 KiB array in device memory that every GPU which
+ * loads libifdlbm.so holds until the process exits.
+ *
+ *  nx, ny   field size; nx * ny <= IFDLBM_STATIC_MAX_NODES, larger fields
+ *           are rejected with IFDLBM_ERR_INVALID_ARG and a message
+ *  u1, v1, p1  DEVICE arrays of nx*ny doubles: u, v, P at step n
+ *  u0, v0, p0  DEVICE arrays of nx*ny doubles: u, v, P at step n-1
+ *  out      DEVICE array of 3 doubles, written with E(u), E(P) of Eq. (2.19)
+ *           and max|u^n - u^(n-1)| / max|u^n| (the same three values
+ *           ifdlbm_residual returns for a handle's last step)
+ *  stream   cudaStream_t the two kernels are enqueued on; the call does not
+ *           synchronise
+ * It works on the calling thread's current device. The first call on each
+ * device looks up the scratch array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture on that device. Every
+ * call shares the one array, and each call writes every partial it reads
+ * (nothing carries over between calls); calls that overlap on the GPU (on
+ * different streams, or from different threads) race on it and must be
+ * serialised by the caller. */
+#define IFDLBM_STATIC_MAX_NODES 2097152
+int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double *v1,
+                                  const double *p1, const double *u0, const double *v0,
+                                  const double *p0, double *out, void *stream);
+
 /* Number of kernel launches the library has enqueued since the process
  * started (graph replays count every kernel node). */
 int64_t ifdlbm_launch_count(void);

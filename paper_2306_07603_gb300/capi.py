@@ -33,6 +33,7 @@ IFDLBM_KPROF_FULL = 2
 IFDLBM_KPROF_REDUCE = 3
 IFDLBM_KPROF_FUSED = 4
 IFDLBM_KPROF_COUNT = 5
+IFDLBM_STATIC_MAX_NODES = 2097152
 
 
 class ifdlbm_geometry(C.Structure):
@@ -87,6 +88,8 @@ _SIGS = {
     "ifdlbm_destroy": (C.c_int, [_H]),
     "ifdlbm_last_error": (C.c_char_p, [_H]),
     "ifdlbm_launch_count": (C.c_int64, []),
+    "ifdlbm_residual_fields_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
+                                                C.c_void_p]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
     "ifdlbm_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -256,6 +259,13 @@ def ifdlbm_last_error(h=None) -> str:
 
 def ifdlbm_launch_count() -> int:
     return int(load_library().ifdlbm_launch_count())
+
+
+def ifdlbm_residual_fields_static(nx, ny, u1, v1, p1, u0, v0, p0, out, stream=0):
+    """Eq. (2.19) residuals of caller-owned device fields; allocates nothing."""
+    return _check(load_library().ifdlbm_residual_fields_static(
+        int(nx), int(ny), _ptr(u1), _ptr(v1), _ptr(p1), _ptr(u0), _ptr(v0), _ptr(p0), _ptr(out),
+        C.c_void_p(int(stream))))
 
 
 def ifdlbm_profile(h, enable):

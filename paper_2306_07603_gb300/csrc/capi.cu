@@ -222,6 +222,9 @@ bool cavity_ok(ifdlbm_ctx *h, int cavity) { return h && cavity >= 0 && cavity < 
 
 }  // namespace
 
+int ifd::set_global_error(int code, const std::string &msg) { return fail(nullptr, code, msg); }
+void ifd::count_launches(int64_t n) { g_launches += n; }
+
 extern "C" {
 
 int ifdlbm_set_allocator(ifdlbm_alloc_fn alloc, ifdlbm_free_fn free_fn, void *ctx) {

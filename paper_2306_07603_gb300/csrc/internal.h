@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/ifdlbm.h).
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 namespace ifd {
@@ -84,6 +85,11 @@ template <class T> void launch_export(const CavDev *cav, int cavity, const void 
 template <class T> void launch_import(const CavDev *cav, int cavity, void *g, double *lam,
                                       const double *fhat, const double *lami, int nx, int ny,
                                       cudaStream_t s);
+
+// Records `msg` as the handle-less last error (ifdlbm_last_error(NULL)) and
+// returns `code`; counts kernel launches for ifdlbm_launch_count (capi.cu).
+int set_global_error(int code, const std::string &msg);
+void count_launches(int64_t n);
 
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 8;
