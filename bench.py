@@ -156,13 +156,21 @@ class ClockSampler:
 # ncu-derived DRAM traffic (profiles/traffic.json), valid only for the
 # kernel source it was taken from
 # ---------------------------------------------------------------------------
-def kernel_source_digest():
+KERNEL_SOURCES = {
+    "fused": ["fused.cu", "d2q9.cuh", "fastpow.cuh", "reduce.cuh", "internal.h"],
+    "collide": ["staged.cu", "d2q9.cuh", "fastpow.cuh", "reduce.cuh", "internal.h"],
+    "half": ["staged.cu", "d2q9.cuh", "fastpow.cuh", "reduce.cuh", "internal.h"],
+    "full": ["staged.cu", "d2q9.cuh", "fastpow.cuh", "reduce.cuh", "internal.h"],
+}
+
+
+def kernel_source_digest(kernel="fused"):
+    """Digest of the device sources a kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_07603_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in KERNEL_SOURCES.get(kernel, sorted(os.listdir(csrc))):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 
@@ -172,7 +180,7 @@ def traffic_per_launch(kernel, precision, lu_per_launch):
         with open(path) as f:
             d = json.load(f)
         e = d[f"{kernel}:{precision}"]
-        if e.get("src_digest") != kernel_source_digest():
+        if e.get("src_digest") != kernel_source_digest(kernel):
             return None
         return float(e["bytes_per_lu"]) * lu_per_launch
     except Exception:

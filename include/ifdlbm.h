@@ -73,14 +73,18 @@ typedef struct {
   double cfl;       /* Courant number, 0.5 (Sec. 5.1) */
   double c;         /* lattice speed, 1.0 (Sec. 5.1) */
   double eta_b;     /* blend of Eq. (2.5) in [0, 1]; default 0.5 */
-  double gamma_min; /* zero-shear clamp of |gamma-dot|; <= 0 means 1e-3 U/H */
+  double gamma_min; /* zero-shear clamp of |gamma-dot|; <= 0 means 1e-3 U/H;
+                       otherwise >= 1e-100 */
   double dt;        /* time step; <= 0 means cfl * min(L/(nx-1), H/(ny-1)) / c */
   double rho0;      /* reference density, 1.0 */
   int precision;    /* IFDLBM_FP64 (default) or IFDLBM_FP32DEV */
   int kernel;       /* IFDLBM_KERNEL_*; default AUTO */
   int graph_chunk;  /* steps per captured CUDA graph, even, >= 2; default 32;
                        0 disables graph capture */
-  int reserved;
+  int fused_threads; /* FUSED: threads per CTA, 64, 128 or 256 (256: FP32DEV
+                        only); each CTA owns at most fused_threads - 8
+                        columns; 0 = 128 */
+  int fused_rows;    /* FUSED: rows per CTA task (>= 2); 0 = automatic */
 } ifdlbm_options;
 
 /* One cavity of a batch (pattern "batching"). */
@@ -259,6 +263,12 @@ int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *
 int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double *v1,
                                   const double *p1, const double *u0, const double *v0,
                                   const double *p0, double *out, void *stream);
+
+/* Self-test of the FP64 power used for Eq. (1.4): for n DEVICE doubles x
+ * (finite, > 0) writes fast[k] = the library's table-driven x^m and
+ * ref[k] = CUDA's pow(x[k], m), on the handle's stream (no sync). */
+int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
+                        double *ref);
 
 /* Number of kernel launches the library has enqueued since the process
  * started (graph replays count every kernel node). */

@@ -44,7 +44,7 @@ class ifdlbm_options(C.Structure):
     _fields_ = [("cfl", C.c_double), ("c", C.c_double), ("eta_b", C.c_double),
                 ("gamma_min", C.c_double), ("dt", C.c_double), ("rho0", C.c_double),
                 ("precision", C.c_int), ("kernel", C.c_int), ("graph_chunk", C.c_int),
-                ("reserved", C.c_int)]
+                ("fused_threads", C.c_int), ("fused_rows", C.c_int)]
 
 
 class ifdlbm_cavity(C.Structure):
@@ -90,6 +90,7 @@ _SIGS = {
     "ifdlbm_launch_count": (C.c_int64, []),
     "ifdlbm_residual_fields_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                 C.c_void_p]),
+    "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
     "ifdlbm_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -266,6 +267,11 @@ def ifdlbm_residual_fields_static(nx, ny, u1, v1, p1, u0, v0, p0, out, stream=0)
     return _check(load_library().ifdlbm_residual_fields_static(
         int(nx), int(ny), _ptr(u1), _ptr(v1), _ptr(p1), _ptr(u0), _ptr(v0), _ptr(p0), _ptr(out),
         C.c_void_p(int(stream))))
+
+
+def ifdlbm_selftest_pow(h, x, m, fast, ref):
+    return _check(load_library().ifdlbm_selftest_pow(h, int(x.numel()), _ptr(x), float(m),
+                                                     _ptr(fast), _ptr(ref)), h)
 
 
 def ifdlbm_profile(h, enable):

@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "fastpow.cuh"
 #include "ifdlbm.h"
 #include "internal.h"
 
@@ -40,6 +41,9 @@ struct ifdlbm_ctx {
   std::vector<double> courant;
   ifd::Bufs b{};
   int ntiles = 0;
+  int ntasks = 0;      // fused kernel tasks
+  int fused_nt = 128;  // fused kernel threads per CTA
+  ifd::Task *tasks = nullptr;
   int64_t total_plane = 0;
   int64_t geo_len = 0;
   int64_t max_n2 = 0;
@@ -158,6 +162,26 @@ void timed(ifdlbm_ctx *h, int kernel, F &&launch) {
 
 template <class T>
 void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
+  if (h->kernel == IFDLBM_KERNEL_FUSED) {
+    ifd::FusedArgs f{};
+    f.cav = h->b.cav;
+    f.geo = h->b.geo;
+    f.tasks = h->tasks;
+    f.g_in = h->b.g[parity];
+    f.g_out = h->b.g[parity ^ 1];
+    f.lam_in = h->b.lam[parity];
+    f.lam_out = h->b.lam[parity ^ 1];
+    f.part = h->b.part;
+    f.status = h->b.status;
+    f.powtab = h->b.powtab;
+    f.want_residual = want_residual ? 1 : 0;
+    timed(h, IFDLBM_KPROF_FUSED, [&] { ifd::launch_fused<T>(f, h->fused_nt, h->ntasks, h->stream); });
+    if (want_residual)
+      timed(h, IFDLBM_KPROF_REDUCE, [&] {
+        ifd::launch_residual_reduce(h->b.cav, h->b.part, h->b.resid, h->ncav, h->stream);
+      });
+    return;
+  }
   ifd::StepArgs a{};
   a.cav = h->b.cav;
   a.geo = h->b.geo;
@@ -172,6 +196,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
   a.m0 = h->b.m0;
   a.part = h->b.part;
   a.status = h->b.status;
+  a.powtab = h->b.powtab;
   a.want_residual = want_residual ? 1 : 0;
   timed(h, IFDLBM_KPROF_COLLIDE, [&] { ifd::launch_collide<T>(a, h->ntiles, h->stream); });
   timed(h, IFDLBM_KPROF_HALF, [&] { ifd::launch_half<T>(a, h->ntiles, h->stream); });
@@ -189,7 +214,10 @@ void enqueue_step_any(ifdlbm_ctx *h, int parity, bool want_residual) {
     enqueue_step<float>(h, parity, want_residual);
 }
 
-int launches_per_step(bool residual) { return residual ? 4 : 3; }
+int launches_per_step(const ifdlbm_ctx *h, bool residual) {
+  const int base = h->kernel == IFDLBM_KERNEL_FUSED ? 1 : 3;
+  return residual ? base + 1 : base;
+}
 
 int ensure_graph(ifdlbm_ctx *h, int parity) {
   if (h->gexec[parity]) return IFDLBM_OK;
@@ -223,6 +251,18 @@ bool cavity_ok(ifdlbm_ctx *h, int cavity) { return h && cavity >= 0 && cavity < 
 }  // namespace
 
 int ifd::set_global_error(int code, const std::string &msg) { return fail(nullptr, code, msg); }
+
+// Tables of pow_fast, in extended precision on the host: r_j = 1/(1 + (j + 1/2)/256)
+// rounded to double, L_j = -log2(r_j) of that double, T_j = 2^(j/256).
+void ifd::fill_pow_tables(double *tab) {
+  for (int j = 0; j < 256; ++j) {
+    const long double c = 1.0L + (j + 0.5L) / 256.0L;
+    const double r = double(1.0L / c);
+    tab[j] = r;
+    tab[256 + j] = double(-log2l((long double)r));
+    tab[512 + j] = double(exp2l((long double)j / 256.0L));
+  }
+}
 void ifd::count_launches(int64_t n) { g_launches += n; }
 
 extern "C" {
@@ -248,6 +288,8 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   opt->precision = IFDLBM_FP64;
   opt->kernel = IFDLBM_KERNEL_AUTO;
   opt->graph_chunk = 32;
+  opt->fused_threads = 0;
+  opt->fused_rows = 0;
   return IFDLBM_OK;
 }
 
@@ -264,10 +306,18 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     ifdlbm_default_options(&opt);
   if (!(opt.cfl > 0) || !(opt.c > 0) || !(opt.eta_b >= 0 && opt.eta_b <= 1) || !(opt.rho0 > 0))
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: need cfl > 0, c > 0, eta_b in [0,1], rho0 > 0");
+  if (opt.gamma_min > 0 && opt.gamma_min < 1e-100)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: gamma_min must be 0 (default) or >= 1e-100");
   if (opt.precision != IFDLBM_FP64 && opt.precision != IFDLBM_FP32DEV)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown precision");
   if (opt.kernel < IFDLBM_KERNEL_AUTO || opt.kernel > IFDLBM_KERNEL_FUSED)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown kernel");
+  if (!(opt.fused_threads == 0 || opt.fused_threads == 64 || opt.fused_threads == 128 ||
+        (opt.fused_threads == 256 && opt.precision == IFDLBM_FP32DEV)))
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
+                "options: fused_threads must be 0, 64, 128 or (FP32DEV) 256");
+  if (opt.fused_rows < 0 || opt.fused_rows == 1)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_rows must be 0 or >= 2");
   if (opt.graph_chunk < 0 || (opt.graph_chunk % 2) != 0)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: graph_chunk must be 0 or even and > 0");
 
@@ -293,8 +343,11 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->ncav = ncav;
   h->opt = opt;
   h->precision = opt.precision;
-  // The fused kernel is not built yet: every request runs the staged kernels.
-  h->kernel = IFDLBM_KERNEL_STAGED;
+  h->kernel = opt.kernel != IFDLBM_KERNEL_AUTO
+                  ? opt.kernel
+                  : (opt.precision == IFDLBM_FP32DEV ? IFDLBM_KERNEL_FUSED : IFDLBM_KERNEL_STAGED);
+  h->fused_nt = opt.fused_threads ? opt.fused_threads : 128;
+  const bool fused = h->kernel == IFDLBM_KERNEL_FUSED;
   h->stream = (cudaStream_t)stream;
   if (h->stream == nullptr) h->opt.graph_chunk = 0;  // the legacy stream cannot be captured
   h->spec.assign(cavs, cavs + ncav);
@@ -340,6 +393,9 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     cv.H = H;
     cv.rho0 = opt.rho0;
     cv.lam0 = cv.K * std::pow(cv.gmin, cv.nm1) / cv.cs2;
+    cv.gmin2 = cv.gmin * cv.gmin;
+    cv.half_nm1 = 0.5 * cv.nm1;
+    cv.Kics2 = cv.K / cv.cs2;
     h->max_n2 = std::max<int64_t>(h->max_n2, int64_t(s.nx) * s.ny);
     // 1-D metric arrays of Eq. (3.8.2)
     xix.resize(goff), xeH.resize(goff), xxi.resize(goff), xeta.resize(goff);
@@ -371,6 +427,31 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->ntiles = tile0;
   h->total_plane = off;
   h->geo_len = goff;
+  // fused tasks: balanced strips of at most fused_nt - 8 columns, balanced row segments
+  std::vector<ifd::Task> tasks;
+  if (fused) {
+    const int W = h->fused_nt - 8;
+    for (int k = 0; k < ncav; ++k) {
+      CavDev &cv = h->cav[k];
+      const int sx = (cv.nx + W - 1) / W;
+      // automatic segment height: shorter segments give more CTAs to small batches
+      const int hs = opt.fused_rows ? opt.fused_rows : (h->total_plane < (int64_t(8) << 20) ? 32 : 64);
+      const int sy = std::max(1, std::min((cv.ny + hs - 1) / hs, cv.ny / 2));
+      cv.part0 = int(tasks.size());
+      for (int b = 0; b < sy; ++b)
+        for (int a = 0; a < sx; ++a) {
+          ifd::Task t{};
+          t.cav = k;
+          t.i0 = int(int64_t(a) * cv.nx / sx);
+          t.i1 = int(int64_t(a + 1) * cv.nx / sx);
+          t.j0 = int(int64_t(b) * cv.ny / sy);
+          t.j1 = int(int64_t(b + 1) * cv.ny / sy);
+          tasks.push_back(t);
+        }
+      cv.nparts = int(tasks.size()) - cv.part0;
+    }
+    h->ntasks = int(tasks.size());
+  }
 
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
   bool ok = true;
@@ -378,18 +459,26 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     ok &= (h->b.g[p] = A(9 * off * tsize)) != nullptr;
     ok &= (h->b.lam[p] = (double *)A(off * sizeof(double))) != nullptr;
   }
-  ok &= (h->b.fb = A(9 * off * tsize)) != nullptr;
-  ok &= (h->b.fp = A(9 * off * tsize)) != nullptr;
-  ok &= (h->b.fh = A(9 * off * tsize)) != nullptr;
-  ok &= (h->b.m0 = (double *)A(3 * off * sizeof(double))) != nullptr;
-  ok &= (h->b.part = (double *)A(size_t(h->ntiles) * ifd::NPART * sizeof(double))) != nullptr;
+  if (!fused) {  // scratch planes of the staged kernels
+    ok &= (h->b.fb = A(9 * off * tsize)) != nullptr;
+    ok &= (h->b.fp = A(9 * off * tsize)) != nullptr;
+    ok &= (h->b.fh = A(9 * off * tsize)) != nullptr;
+    ok &= (h->b.m0 = (double *)A(3 * off * sizeof(double))) != nullptr;
+  } else {
+    ok &= (h->tasks = (ifd::Task *)A(tasks.size() * sizeof(ifd::Task))) != nullptr;
+  }
+  const int nslots = fused ? h->ntasks : h->ntiles;
+  ok &= (h->b.part = (double *)A(size_t(nslots) * ifd::NPART * sizeof(double))) != nullptr;
   ok &= (h->b.resid = (double *)A(size_t(ncav) * 4 * sizeof(double))) != nullptr;
   ok &= (h->b.tile_cav = (int *)A(size_t(h->ntiles) * sizeof(int))) != nullptr;
   ok &= (h->b.status = (unsigned *)A(sizeof(unsigned))) != nullptr;
   ok &= (h->b.cav = (CavDev *)A(size_t(ncav) * sizeof(CavDev))) != nullptr;
   double *geo = (double *)A(size_t(4 * goff) * sizeof(double));
   ok &= geo != nullptr;
+  float *geof = (float *)A(size_t(2 * goff) * sizeof(float));
+  ok &= geof != nullptr;
   ok &= (h->stage = (double *)A(size_t(10 * h->max_n2) * sizeof(double))) != nullptr;
+  ok &= (h->b.powtab = (double *)A(ifd::POW_TABLE_SIZE * sizeof(double))) != nullptr;
   if (!ok) {
     release_all(h);
     delete h;
@@ -399,6 +488,16 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->b.geo.xeH = geo + goff;
   h->b.geo.xxi = geo + 2 * goff;
   h->b.geo.xeta = geo + 3 * goff;
+  h->b.geo.cxix_f = geof;
+  h->b.geo.jac_f = geof + goff;
+  std::vector<float> geof_h(2 * goff);
+  for (int k = 0; k < ncav; ++k) {
+    const CavDev &cv = h->cav[k];
+    for (int j = 0; j < cv.ny; ++j) {
+      geof_h[cv.goff + j] = float(cv.c * xix[cv.goff + j]);
+      geof_h[goff + cv.goff + j] = float(xxi[cv.goff + j] * cv.H);
+    }
+  }
 
   std::vector<int> tile_cav(h->ntiles);
   for (int k = 0; k < ncav; ++k)
@@ -411,7 +510,8 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
 
   cudaStream_t s = h->stream;
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
-                         geo_h.size() * sizeof(double));
+                         geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
+                         ifd::POW_TABLE_SIZE * sizeof(double));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -419,10 +519,26 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(geo, geo_h.data(), geo_h.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(geof, geof_h.data(), geof_h.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        s);
+  static std::vector<double> powtab_h = [] {
+    std::vector<double> t(ifd::POW_TABLE_SIZE);
+    ifd::fill_pow_tables(t.data());
+    return t;
+  }();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.powtab, powtab_h.data(), powtab_h.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
   // every buffer starts zeroed so that no read can ever see uninitialised memory
   for (void *ptr : {h->b.fb, h->b.fp, h->b.fh, h->b.g[1]})
-    if (e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, 9 * off * tsize, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.m0, 0, 3 * off * sizeof(double), s);
+    if (ptr && e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, 9 * off * tsize, s);
+  if (h->b.m0 && e == cudaSuccess) e = cudaMemsetAsync(h->b.m0, 0, 3 * off * sizeof(double), s);
+  if (fused && e == cudaSuccess) {
+    e = cudaMemcpyAsync(h->tasks, tasks.data(), tasks.size() * sizeof(ifd::Task),
+                        cudaMemcpyHostToDevice, s);
+    h->h2d_bytes += int64_t(tasks.size() * sizeof(ifd::Task));
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.status, 0, sizeof(unsigned), s);
@@ -471,19 +587,19 @@ int ifdlbm_step(ifdlbm_handle h, int nsteps) {
       if (rc) return rc;
       cudaError_t e = cudaGraphLaunch(h->gexec[h->cur], h->stream);
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphLaunch");
-      g_launches += int64_t(chunk) * launches_per_step(false);
+      g_launches += int64_t(chunk) * launches_per_step(h, false);
       remaining -= chunk;
       h->steps += chunk;
     }
   }
   for (; remaining > 0; --remaining) {
     enqueue_step_any(h, h->cur, false);
-    g_launches += launches_per_step(false);
+    g_launches += launches_per_step(h, false);
     h->cur ^= 1;
     h->steps += 1;
   }
   enqueue_step_any(h, h->cur, true);
-  g_launches += launches_per_step(true);
+  g_launches += launches_per_step(h, true);
   h->cur ^= 1;
   h->steps += 1;
   cudaError_t e = cudaGetLastError();
@@ -664,6 +780,19 @@ const char *ifdlbm_last_error(ifdlbm_handle h) {
 }
 
 int64_t ifdlbm_launch_count(void) { return g_launches.load(); }
+
+int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
+                        double *ref) {
+  if (!h || n < 0 || (n > 0 && (!x || !fast || !ref)))
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "selftest_pow: bad arguments");
+  if (n == 0) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  ifd::launch_pow_selftest(n, x, m, h->b.powtab, fast, ref, h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "selftest_pow");
+  return IFDLBM_OK;
+}
 
 int ifdlbm_profile(ifdlbm_handle h, int enable) {
   if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");

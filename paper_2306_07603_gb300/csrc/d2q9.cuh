@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "fastpow.cuh"
 #include "internal.h"
 
 namespace ifd {
@@ -56,18 +57,20 @@ __device__ __forceinline__ void equilibrium(T P, T ux, T uy, T c, T inv_cs2, T g
 }
 
 // Relaxation time of Step (2): strain rate from f^ne (Eqs. 2.12-2.13, with
-// f = f(f-hat, lam_prev) of Eq. 2.18), |gamma-dot| = sqrt(2 D:D), the
-// clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) (Eq. 1.4) and
-// lam = mu / c_s^2 (Eq. 2.14). Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i).
-// Always FP64.
-__device__ __forceinline__ double relaxation_time(double Pxx, double Pxy, double Pyy,
-                                                  double lam_prev, const CavDev &cv) {
+// f = f(f-hat, lam_prev) of Eq. 2.18), q = |gamma-dot|^2 = 2 D:D, the
+// clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) evaluated as
+// K max(q, gamma_min^2)^((n-1)/2) (Eq. 1.4), and lam = mu / c_s^2 (Eq. 2.14).
+// Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i). The strain rate is formed
+// in T (the storage precision); the power law is always evaluated in FP64.
+template <class T>
+__device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
+                                                  const CavDev &cv, const double *powtab) {
   // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
-  const double k = -2.0 / ((2.0 * lam_prev + cv.dt) * cv.cs2);
-  const double Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;
-  double gd = sqrt(0.5 * (Sxx * Sxx + 2.0 * Sxy * Sxy + Syy * Syy));
-  gd = gd > cv.gmin ? gd : cv.gmin;
-  return cv.K * pow(gd, cv.nm1) * cv.inv_cs2;
+  const T k = T(-2) / ((T(2) * T(lam_prev) + T(cv.dt)) * T(cv.cs2));
+  const T Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;
+  double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+  q = q > cv.gmin2 ? q : cv.gmin2;
+  return cv.Kics2 * pow_fast(q, cv.half_nm1, powtab);
 }
 
 // Second moments of the non-equilibrium deviation d_i = g_i - geq_i.
@@ -104,6 +107,19 @@ __device__ __forceinline__ T dmix2(T fm2, T fm1, T f0, T fp1, T fp2, bool pos, b
 __device__ __forceinline__ double cxi_of(int q, double A, double B) {
   // A = c xi_x, B = c xi_x x_eta / H
   return double(ex(q)) * A - double(ey(q)) * B;
+}
+
+// Wall-node rule (Sec. 4): F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
+template <class T>
+__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
+  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
+  T ux, uy, P;
+  moments(F, c, cs2, ux, uy, P);
+  T fw[9], fn[9];
+  equilibrium(P, uwx, uwy, c, ics2, fw);
+  equilibrium(P, ux, uy, c, ics2, fn);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = fw[q] + (F[q] - fn[q]);
 }
 
 }  // namespace ifd

@@ -24,6 +24,9 @@ struct CavDev {
   double inv2dxi, inv2deta; // 1/(2 dxi), 1/(2 deta)
   double U, H, rho0;        // lid speed, height, reference density
   double lam0;              // Eq. (2.14) at zero shear (initial lambda_prev)
+  double gmin2;             // gamma_min^2
+  double half_nm1;          // (n - 1) / 2: mu = K max(q, gamma_min^2)^((n-1)/2), q = gamma-dot^2
+  double Kics2;             // K / c_s^2
 };
 
 // 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
@@ -31,8 +34,11 @@ struct CavDev {
 //   xeH[i]  = x_eta(xi_i) / H                           (nx entries)
 //   xxi[j]  = x_xi(eta_j)    (Jacobian J = x_xi * H)    (ny entries)
 //   xeta[i] = x_eta(xi_i)    (stream function)          (nx entries)
+//   cxix_f[j] = float(c xi_x(eta_j)), jac_f[j] = float(x_xi(eta_j) H): rounded
+//   copies used only where the arithmetic is FP32 (fused FP32 kernel)
 struct Geo {
   const double *xix, *xeH, *xxi, *xeta;
+  const float *cxix_f, *jac_f;
 };
 
 // Device buffers of a handle. T is double (FP64) or float (FP32DEV).
@@ -49,6 +55,7 @@ struct Bufs {
   unsigned *status;  // bit 0: non-finite velocity seen
   CavDev *cav;       // [ncav]
   Geo geo;
+  double *powtab;    // tables of pow_fast (fastpow.cuh)
 };
 
 struct StepArgs {
@@ -63,8 +70,33 @@ struct StepArgs {
   double *m0;
   double *part;
   unsigned *status;
+  const double *powtab;
   int want_residual;
 };
+
+// One CTA task of the fused kernel: owned columns [i0, i1) (at most NT - 8)
+// and rows [j0, j1) of cavity `cav`.
+struct Task {
+  int cav, i0, i1, j0, j1, pad0, pad1, pad2;
+};
+
+struct FusedArgs {
+  const CavDev *cav;
+  Geo geo;
+  const Task *tasks;
+  const void *g_in;
+  void *g_out;
+  const double *lam_in;
+  double *lam_out;
+  double *part;
+  unsigned *status;
+  const double *powtab;
+  int want_residual;
+};
+
+// Fused kernel (fused.cu); nt in {64, 128, 256} (256 in FP32 only).
+template <class T> bool launch_fused(const FusedArgs &a, int nt, int ntasks, cudaStream_t s);
+template <class T> int fused_smem_bytes(int nt);
 
 // Staged kernels (staged.cu)
 template <class T> void launch_collide(const StepArgs &a, int ntiles, cudaStream_t s);
@@ -72,6 +104,11 @@ template <class T> void launch_half(const StepArgs &a, int ntiles, cudaStream_t 
 template <class T> void launch_full(const StepArgs &a, int ntiles, cudaStream_t s);
 void launch_residual_reduce(const CavDev *cav, const double *part, double *resid, int ncav,
                             cudaStream_t s);
+
+// Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
+void fill_pow_tables(double *tab);
+void launch_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
+                         double *ref, cudaStream_t s);
 
 // Utility kernels (staged.cu)
 template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,

@@ -42,6 +42,27 @@ __device__ __forceinline__ void block_partial(Partial p, double *part, int slot)
   }
 }
 
+// Adds one node's terms of Eq. (2.19) (new vs old u, v, P) and of Eq. (5.1)
+// (composite trapezoidal weights, Jacobian x_xi H) to p; flags a non-finite
+// velocity in the status word.
+__device__ __forceinline__ void accumulate_residual(Partial &p, double u1, double v1, double P1,
+                                                    double u0, double v0, double P0, int i, int j,
+                                                    const CavDev &cv, const Geo &geo,
+                                                    unsigned *status) {
+  if (!(isfinite(u1) && isfinite(v1))) atomicOr(status, 1u);
+  const double du = u1 - u0, dv = v1 - v0, dP = P1 - P0;
+  const double du2 = du * du + dv * dv, u2 = u1 * u1 + v1 * v1;
+  p.du2 += du2;
+  p.u2 += u2;
+  p.dP2 += dP * dP;
+  p.P2 += P1 * P1;
+  p.du2max = fmax(p.du2max, du2);
+  p.u2max = fmax(p.u2max, u2);
+  const double wx = ((i == 0 || i == cv.nx - 1) ? 0.5 : 1.0) * cv.dxi;
+  const double wy = ((j == 0 || j == cv.ny - 1) ? 0.5 : 1.0) * cv.deta;
+  p.ek += 0.5 * wx * wy * (geo.xxi[cv.goff + j] * cv.H) * u2;
+}
+
 // One block of 256 threads: sums slots [0, nslots) of `part` in a fixed
 // order and writes out[0] = E(u), out[1] = E(P) (Eq. 2.19), out[2] = the
 // max-norm velocity residual, out[3] = the kinetic-energy sum (Eq. 5.1).

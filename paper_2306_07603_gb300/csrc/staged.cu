@@ -80,13 +80,13 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_collide(StepArgs a) {
   for (int q = 0; q < 9; ++q) d[q] = g[q] - geq[q];
   T pxx, pxy, pyy;
   second_moments(d, c, pxx, pxy, pyy);
-  const double lam = relaxation_time(double(pxx), double(pxy), double(pyy), lam_prev, cv);
+  const double lam = relaxation_time(pxx, pxy, pyy, lam_prev, cv, a.powtab);
   a.lam_out[cv.off + node] = lam;                // lam(t), also next lam_prev
 
   const T L = T(lam), dt = T(cv.dt);
   const T i2 = T(1) / (T(2) * L + dt);
   const T ap = (T(2) * L - dt) * i2, bp = T(2) * dt * i2;     // Eq. (2.15)
-  const T i4 = T(1) / (T(4) * L + T(2) * dt);
+  const T i4 = T(0.5) * i2;                                   // 1 / (4 lam + 2 dt)
   const T ab = (T(4) * L - dt) * i4, bb = T(3) * dt * i4;     // Eq. (2.16)
   T *fp = (T *)a.fp + b9;
   T *fb = (T *)a.fb + b9;
@@ -117,19 +117,6 @@ __device__ __forceinline__ T advect(const T *F, int64_t node, int pitch, int i, 
   const T deta = dmix2(F[node + jm2 * p], F[node - p], f0, F[node + p], F[node + jp2 * p],
                        ceta >= T(0), j == 1, j == ny - 2, eta_b) * T(cv.inv2deta);
   return cxi * dxi + ceta * deta;
-}
-
-// Wall-node rule (Sec. 4): F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
-template <class T>
-__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
-  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
-  T ux, uy, P;
-  moments(F, c, cs2, ux, uy, P);
-  T fw[9], fn[9];
-  equilibrium(P, uwx, uwy, c, ics2, fw);
-  equilibrium(P, ux, uy, c, ics2, fn);
-#pragma unroll
-  for (int q = 0; q < 9; ++q) F[q] = fw[q] + (F[q] - fn[q]);
 }
 
 __device__ __forceinline__ void wall_neighbour(const CavDev &cv, int i, int j, int &ii, int &jj,
@@ -318,6 +305,19 @@ __global__ void k_import(const CavDev *cavs, int cavity, T *g, double *lam, cons
   for (int q = 0; q < 9; ++q)
     g[9 * cv.off + q * cv.plane + node] = T(fhat[q * n2 + o] - wgt(q) * cv.rho0);
   lam[cv.off + node] = lami[o];
+}
+
+__global__ void k_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
+                               double *ref) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  fast[k] = pow_fast(x[k], m, tab);
+  ref[k] = pow(x[k], m);
+}
+
+void launch_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
+                         double *ref, cudaStream_t s) {
+  k_pow_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, tab, fast, ref);
 }
 
 // ---------------------------------------------------------------------------

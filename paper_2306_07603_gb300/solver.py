@@ -16,12 +16,13 @@ _KERN = {"auto": capi.IFDLBM_KERNEL_AUTO, "staged": capi.IFDLBM_KERNEL_STAGED,
 
 
 def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, dt=None,
-                 gamma_min=None, graph_chunk=None):
+                 gamma_min=None, graph_chunk=None, fused_threads=None, fused_rows=None):
     opt = capi.ifdlbm_default_options()
     opt.precision = _PREC[precision]
     opt.kernel = _KERN[kernel]
     for name, val in (("eta_b", eta_b), ("cfl", cfl), ("c", c), ("dt", dt),
-                      ("gamma_min", gamma_min), ("graph_chunk", graph_chunk)):
+                      ("gamma_min", gamma_min), ("graph_chunk", graph_chunk),
+                      ("fused_threads", fused_threads), ("fused_rows", fused_rows)):
         if val is not None:
             setattr(opt, name, val)
     return opt

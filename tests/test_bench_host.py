@@ -66,5 +66,6 @@ def test_reference_arm_json_contract():
 
 def test_kernel_digest_changes_with_source(tmp_path):
     import bench
-    d1 = bench.kernel_source_digest()
-    assert len(d1) == 16 and d1 == bench.kernel_source_digest()
+    d1 = bench.kernel_source_digest("fused")
+    assert len(d1) == 16 and d1 == bench.kernel_source_digest("fused")
+    assert d1 != bench.kernel_source_digest("collide")

@@ -89,13 +89,23 @@ CASES = [
 ]
 
 
+# kernel organisations: staged; fused with several CTA widths and row segments
+# (small segments put task boundaries inside the grid)
+KERNELS = {
+    "staged": dict(kernel="staged"),
+    "fused64x8": dict(kernel="fused", fused_threads=64, fused_rows=8),
+    "fused128": dict(kernel="fused", fused_threads=128),
+}
+
+
+@pytest.mark.parametrize("kname", list(KERNELS))
 @pytest.mark.parametrize("nx,ny,Re,n,th,k0", CASES)
-def test_one_step_fp64_parity(nx, ny, Re, n, th, k0):
+def test_one_step_fp64_parity(nx, ny, Re, n, th, k0, kname):
     run = oracle_run(nx, ny, Re, n, th)
     run.advance(k0)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     fo, lo = O.step(f0, l0, run.g, run.prm)
-    s = solver([cav(nx, ny, Re, n, th)])
+    s = solver([cav(nx, ny, Re, n, th)], **KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)
@@ -118,11 +128,12 @@ def test_rest_start_matches_oracle_initial_state():
     compare_state(fg, lg, run.fhat, run.lam, tol=1e-15)
 
 
-def test_config1_4000_steps_fields_and_residual_history():
+@pytest.mark.parametrize("kname", ["staged", "fused64x8"])
+def test_config1_4000_steps_fields_and_residual_history(kname):
     """65^2, theta = 60 deg, n = 0.75, Re = 100, 4000 steps from rest:
     rho, u, v, psi and the residual every 500 steps."""
     run = oracle_run(65, 65, 100.0, 0.75, 60.0)
-    s = solver([cav(65, 65, 100.0, 0.75, 60.0)])
+    s = solver([cav(65, 65, 100.0, 0.75, 60.0)], **KERNELS[kname])
     for k in range(8):
         run.advance(499)
         f_in, l_in = run.fhat.copy(), run.lam.copy()
@@ -141,10 +152,11 @@ def test_config1_4000_steps_fields_and_residual_history():
         assert np.abs(mg[k] - mo[k]).max() <= TOL64 * np.abs(mo[k]).max(), k
 
 
-def test_batch_of_uneven_cavities_matches_each_oracle():
+@pytest.mark.parametrize("kname", list(KERNELS))
+def test_batch_of_uneven_cavities_matches_each_oracle(kname):
     specs = [(67, 45, 100.0, 0.75, 60.0), (33, 29, 1000.0, 0.5, 45.0), (41, 57, 400.0, 1.5, 75.0),
              (5, 5, 100.0, 1.0, 90.0)]
-    s = solver([cav(*sp) for sp in specs])
+    s = solver([cav(*sp) for sp in specs], **KERNELS[kname])
     runs = []
     for k, sp in enumerate(specs):
         r = oracle_run(*sp)
@@ -184,14 +196,15 @@ def test_eta_b_and_dt_options_reach_the_kernel():
     compare_state(fg, lg, run.fhat, run.lam, lam_tol=lam_bound(f_in, l_in, run.prm, run.lam))
 
 
-def test_fp32_deviation_one_step_error():
+@pytest.mark.parametrize("kname", list(KERNELS))
+def test_fp32_deviation_one_step_error(kname):
     """FP32 deviation storage: one step from an oracle state stays within
     1e-5 relative of the FP64 oracle on every field."""
     run = oracle_run(67, 45, 100.0, 0.75, 60.0)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     fo, lo = O.step(f0, l0, run.g, run.prm)
-    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev")
+    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev", **KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)

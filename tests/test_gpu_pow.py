@@ -1,0 +1,55 @@
+"""The FP64 power of the power-law viscosity (Eq. 1.4) against CUDA's pow.
+
+The library evaluates max(q, gamma_min^2)^((n-1)/2) with a table-driven
+method (Tang, ACM TOMS 1989/1990). Over the range the power law meets
+(q = |gamma-dot|^2 in [1e-12, 1e8], exponents (n-1)/2 for n in (0, 3]) its
+relative error from CUDA's pow must stay within the bound derived from its
+roundings, 5e-16 + 2.2e-16 |m log2 x| (log2 x and m log2 x are single
+doubles), and the Newtonian exponent 0 must give exactly 1.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def handle():
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    s = Solver([cavity(9, 9, 100.0, 0.75)])
+    yield s
+    s.close()
+
+
+def _run(s, x, m):
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    xd = torch.as_tensor(x, dtype=torch.float64, device="cuda")
+    fast = torch.empty_like(xd)
+    ref = torch.empty_like(xd)
+    capi.ifdlbm_selftest_pow(s.h, xd, m, fast, ref)
+    s.stream.synchronize()
+    return fast.cpu().numpy(), ref.cpu().numpy()
+
+
+@pytest.mark.parametrize("m", [-0.5, -0.375, -0.25, -0.125, 0.125, 0.25, 0.5, 0.73, 1.0])
+def test_pow_fast_relative_error(handle, m):
+    rng = np.random.default_rng(12345)
+    x = 10.0 ** rng.uniform(-12, 8, size=200000)
+    # table-cell boundaries and exact powers of two
+    j = np.arange(256)
+    edges = np.concatenate([1 + j / 256.0, 1 + (j + 0.5) / 256.0, np.nextafter(1 + j / 256.0, 0)])
+    x = np.concatenate([x, edges, edges * 2.0 ** -20, 2.0 ** np.arange(-40, 27)])
+    fast, ref = _run(handle, x, m)
+    bound = 5e-16 + 2.2e-16 * np.abs(m * np.log2(x))
+    rel = np.abs(fast - ref) / np.abs(ref)
+    assert np.all(rel <= bound), (m, (rel / bound).max(), x[np.argmax(rel / bound)])
+    rel_np = np.abs(fast - np.power(x, m)) / np.power(x, m)
+    assert np.all(rel_np <= bound + 2.3e-16)
+
+
+def test_pow_fast_newtonian_exponent_is_exactly_one(handle):
+    x = 10.0 ** np.linspace(-12, 8, 1001)
+    fast, _ = _run(handle, x, 0.0)
+    assert np.all(fast == 1.0)
