@@ -59,6 +59,8 @@ def parse_args(argv=None):
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip the adjoint measurement (257^2, 2000 steps, checkpoints every 100)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU work budget of the oracle baseline sample")
     return p.parse_args(argv)
@@ -347,12 +349,54 @@ def run_ours(args):
             "e2e": e2e,
             "last_residual_cavity0": [float(x) for x in resid[0]],
         }
+        if world == 1 and not args.no_adjoint:
+            out["adjoint"] = run_adjoint_measure()
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(specs, args.cpu_seconds)
     s.close()
     if world > 1:
         dist.destroy_process_group()
     return out
+
+
+def run_adjoint_measure(nx=257, ny=257, T=2000, every=100, n=0.75, Re=400.0, theta=60.0):
+    """Time and memory of d E(T) / d(n, Re, theta) through the hand-written
+    adjoint against the plain FP64 forward run of the same T steps."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.adjoint import KineticEnergy
+    from paper_2306_07603_gb300.solver import Solver, cavity
+
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=theta)], precision="fp64", kernel="staged")
+    s.step(2)
+    s.sync()
+    t0 = time.perf_counter()
+    s.step(T)
+    s.sync()
+    t_plain = time.perf_counter() - t0
+    state_bytes = capi.ifdlbm_state_bytes(s.h)
+    handle_bytes = capi.ifdlbm_info(s.h, 0).device_bytes
+    s.close()
+    p = torch.tensor([n, Re, theta], dtype=torch.float64, requires_grad=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J = KineticEnergy.apply(p, nx, ny, T, every)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    J.backward()
+    torch.cuda.synchronize()
+    t_bwd = time.perf_counter() - t0
+    ckpt = (T + every - 1) // every + 1
+    return {"workload": f"{nx}x{ny}, theta={theta:g}, n={n:g}, Re={Re:g}, {T} steps, FP64, "
+                        f"checkpoint every {every}",
+            "plain_forward_s": round(t_plain, 4), "forward_with_checkpoints_s": round(t_fwd, 4),
+            "backward_s": round(t_bwd, 4), "gradient_over_forward": round((t_fwd + t_bwd) / t_plain, 2),
+            "checkpoint_bytes": ckpt * state_bytes, "segment_bytes": every * state_bytes,
+            "handle_bytes": handle_bytes, "adjoint_scratch_bytes": 4 * 9 * state_bytes // 10,
+            "dJ": {"n": float(p.grad[0]), "Re": float(p.grad[1]), "theta_deg": float(p.grad[2])},
+            "J": float(J.detach())}
 
 
 def run_e2e(args, specs, stream, world):

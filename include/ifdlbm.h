@@ -264,6 +264,27 @@ int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double
                                   const double *p1, const double *u0, const double *v0,
                                   const double *p0, double *out, void *stream);
 
+/* Discrete adjoint (reverse mode) of the step, for gradients of a scalar
+ * objective with respect to n, Re and theta (pattern "differentiation").
+ * Needs a handle created with IFDLBM_FP64 and IFDLBM_KERNEL_STAGED. States
+ * and adjoints are DEVICE buffers of ifdlbm_state_bytes(h) bytes in the
+ * layout of ifdlbm_save_state_dev (adjoint entry k is d J / d state entry k).
+ * dparams is a DEVICE array [ncav][3] to which d J / d n, d J / d Re and
+ * d J / d theta_deg (theta in degrees) are ADDED. Asynchronous on the
+ * handle's stream; the first call allocates the adjoint scratch.
+ *
+ * ifdlbm_adjoint_seed_energy: J = the kinetic energy of Eq. (5.1) of every
+ *   cavity at `state` (composite trapezoidal rule, J dxi deta area element);
+ *   writes adj = dJ/dstate and adds the direct theta term (through the
+ *   Jacobian of Eq. 3.3) to dparams.
+ * ifdlbm_adjoint_step: with state_n the state before step n (Steps 2-7) and
+ *   adj the adjoint of the state after it, recomputes step n and replaces adj
+ *   by the adjoint of state_n, adding the step's parameter terms (n and Re
+ *   through K of Eq. 2.15.1 and the exponent of Eq. 1.4; theta through the
+ *   contravariant velocities of Eq. 3.4) to dparams. */
+int ifdlbm_adjoint_seed_energy(ifdlbm_handle h, const void *state, void *adj, double *dparams);
+int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double *dparams);
+
 /* Self-test of the FP64 power used for Eq. (1.4): for n DEVICE doubles x
  * (finite, > 0) writes fast[k] = the library's table-driven x^m and
  * ref[k] = CUDA's pow(x[k], m), on the handle's stream (no sync). */

@@ -91,6 +91,8 @@ _SIGS = {
     "ifdlbm_residual_fields_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                 C.c_void_p]),
     "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
+    "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
+    "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
     "ifdlbm_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
@@ -267,6 +269,15 @@ def ifdlbm_residual_fields_static(nx, ny, u1, v1, p1, u0, v0, p0, out, stream=0)
     return _check(load_library().ifdlbm_residual_fields_static(
         int(nx), int(ny), _ptr(u1), _ptr(v1), _ptr(p1), _ptr(u0), _ptr(v0), _ptr(p0), _ptr(out),
         C.c_void_p(int(stream))))
+
+
+def ifdlbm_adjoint_seed_energy(h, state, adj, dparams):
+    return _check(load_library().ifdlbm_adjoint_seed_energy(h, _ptr(state), _ptr(adj),
+                                                            _ptr(dparams)), h)
+
+
+def ifdlbm_adjoint_step(h, state_n, adj, dparams):
+    return _check(load_library().ifdlbm_adjoint_step(h, _ptr(state_n), _ptr(adj), _ptr(dparams)), h)
 
 
 def ifdlbm_selftest_pow(h, x, m, fast, ref):

@@ -44,6 +44,9 @@ struct ifdlbm_ctx {
   int ntasks = 0;      // fused kernel tasks
   int fused_nt = 128;  // fused kernel threads per CTA
   ifd::Task *tasks = nullptr;
+  // adjoint scratch (allocated on the first adjoint call)
+  double *adj_g1 = nullptr, *adj_l1 = nullptr, *adj_fhb = nullptr, *adj_fbarb = nullptr,
+         *adj_fbb = nullptr, *adj_lamb2 = nullptr, *adj_ppart = nullptr;
   int64_t total_plane = 0;
   int64_t geo_len = 0;
   int64_t max_n2 = 0;
@@ -394,6 +397,12 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     cv.rho0 = opt.rho0;
     cv.lam0 = cv.K * std::pow(cv.gmin, cv.nm1) / cv.cs2;
     cv.gmin2 = cv.gmin * cv.gmin;
+    {
+      const double t = s.geom.theta_deg * (M_PI / 180.0), sn = std::sin(t);
+      cv.dcot = -(M_PI / 180.0) / (sn * sn);
+    }
+    cv.lnHU = std::log(H) - std::log(s.U_lid);
+    cv.Re = s.Re;
     cv.half_nm1 = 0.5 * cv.nm1;
     cv.Kics2 = cv.K / cv.cs2;
     h->max_n2 = std::max<int64_t>(h->max_n2, int64_t(s.nx) * s.ny);
@@ -780,6 +789,97 @@ const char *ifdlbm_last_error(ifdlbm_handle h) {
 }
 
 int64_t ifdlbm_launch_count(void) { return g_launches.load(); }
+
+namespace {
+
+int adjoint_ready(ifdlbm_ctx *h) {
+  if (h->precision != IFDLBM_FP64 || h->kernel != IFDLBM_KERNEL_STAGED)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: needs a FP64 handle with the staged kernels");
+  if (h->adj_g1) return IFDLBM_OK;
+  const size_t P = size_t(h->total_plane) * sizeof(double);
+  bool ok = true;
+  ok &= (h->adj_g1 = (double *)dalloc(h, 9 * P)) != nullptr;
+  ok &= (h->adj_l1 = (double *)dalloc(h, P)) != nullptr;
+  ok &= (h->adj_fhb = (double *)dalloc(h, 9 * P)) != nullptr;
+  ok &= (h->adj_fbarb = (double *)dalloc(h, 9 * P)) != nullptr;
+  ok &= (h->adj_fbb = (double *)dalloc(h, 9 * P)) != nullptr;
+  ok &= (h->adj_lamb2 = (double *)dalloc(h, P)) != nullptr;
+  ok &= (h->adj_ppart = (double *)dalloc(h, size_t(h->ntiles) * 12 * sizeof(double))) != nullptr;
+  if (!ok) return fail(h, IFDLBM_ERR_OOM, "adjoint: device allocation failed");
+  for (double *p : {h->adj_fhb, h->adj_fbarb, h->adj_fbb})
+    cudaMemsetAsync(p, 0, 9 * P, h->stream);
+  cudaMemsetAsync(h->adj_lamb2, 0, P, h->stream);
+  return IFDLBM_OK;
+}
+
+ifd::AdjArgs adj_args(ifdlbm_ctx *h, const void *state, void *adj) {
+  ifd::AdjArgs a{};
+  const int64_t n9 = 9 * h->total_plane;
+  a.cav = h->b.cav;
+  a.geo = h->b.geo;
+  a.tile_cav = h->b.tile_cav;
+  a.g = (const double *)state;
+  a.lam_p = (const double *)state + n9;
+  a.lam = h->adj_l1;
+  a.fb = (const double *)h->b.fb;
+  a.fp = (const double *)h->b.fp;
+  a.fh = (const double *)h->b.fh;
+  a.gn = h->adj_g1;
+  a.adj_g = (double *)adj;
+  a.adj_lam = (double *)adj + n9;
+  a.fhb = h->adj_fhb;
+  a.fbarb = h->adj_fbarb;
+  a.fbb = h->adj_fbb;
+  a.lamb2 = h->adj_lamb2;
+  a.ppart = h->adj_ppart;
+  return a;
+}
+
+}  // namespace
+
+int ifdlbm_adjoint_seed_energy(ifdlbm_handle h, const void *state, void *adj, double *dparams) {
+  if (!h || !state || !adj || !dparams) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  cudaSetDevice(h->device);
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  ifd::launch_adjoint_seed(adj_args(h, state, adj), h->ntiles, h->ncav, dparams, h->stream);
+  g_launches += 2;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint seed");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double *dparams) {
+  if (!h || !state_n || !adj || !dparams) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  cudaSetDevice(h->device);
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  // forward intermediates of step n from state n (staged kernels)
+  ifd::StepArgs f{};
+  f.cav = h->b.cav;
+  f.geo = h->b.geo;
+  f.tile_cav = h->b.tile_cav;
+  f.g_in = state_n;
+  f.lam_in = (const double *)state_n + 9 * h->total_plane;
+  f.g_out = h->adj_g1;
+  f.lam_out = h->adj_l1;
+  f.fb = h->b.fb;
+  f.fp = h->b.fp;
+  f.fh = h->b.fh;
+  f.m0 = h->b.m0;
+  f.part = h->b.part;
+  f.status = h->b.status;
+  f.powtab = h->b.powtab;
+  f.want_residual = 0;
+  ifd::launch_collide<double>(f, h->ntiles, h->stream);
+  ifd::launch_half<double>(f, h->ntiles, h->stream);
+  ifd::launch_full<double>(f, h->ntiles, h->stream);
+  ifd::launch_adjoint_step(adj_args(h, state_n, adj), h->ntiles, h->ncav, dparams, h->stream);
+  g_launches += 3 + 9;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step");
+  return IFDLBM_OK;
+}
 
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
                         double *ref) {

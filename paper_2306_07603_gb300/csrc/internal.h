@@ -27,6 +27,9 @@ struct CavDev {
   double gmin2;             // gamma_min^2
   double half_nm1;          // (n - 1) / 2: mu = K max(q, gamma_min^2)^((n-1)/2), q = gamma-dot^2
   double Kics2;             // K / c_s^2
+  double dcot;              // d cot(theta) / d theta_deg (adjoint)
+  double lnHU;              // ln H - ln U: d ln K / d n (adjoint)
+  double Re;                // Reynolds number (adjoint)
 };
 
 // 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
@@ -104,6 +107,23 @@ template <class T> void launch_half(const StepArgs &a, int ntiles, cudaStream_t 
 template <class T> void launch_full(const StepArgs &a, int ntiles, cudaStream_t s);
 void launch_residual_reduce(const CavDev *cav, const double *part, double *resid, int ncav,
                             cudaStream_t s);
+
+// Discrete adjoint of one staged FP64 step (adjoint.cu). Buffers use the
+// state layout: 9 planes then 1 plane per cavity at the usual offsets.
+struct AdjArgs {
+  const CavDev *cav;
+  Geo geo;
+  const int *tile_cav;
+  const double *g, *lam_p;   // state n
+  const double *lam;         // lambda(t) of step n (forward output)
+  const double *fb, *fp, *fh;  // forward intermediates of step n
+  const double *gn;          // state n + 1 (forward output)
+  double *adj_g, *adj_lam;   // in: adjoint of state n + 1; out: of state n
+  double *fhb, *fbarb, *fbb, *lamb2;  // adjoint scratch
+  double *ppart;             // [ntiles][4 slots][3] parameter partials
+};
+void launch_adjoint_seed(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s);
+void launch_adjoint_step(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s);
 
 // Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
 void fill_pow_tables(double *tab);
