@@ -221,12 +221,47 @@ def cpu_baseline(specs, seconds):
 # ---------------------------------------------------------------------------
 # The GPU arm
 # ---------------------------------------------------------------------------
-def make_solver(specs, precision, kernel, stream=None):
+def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
     from paper_2306_07603_gb300.solver import Solver, cavity
+    from paper_2306_07603_gb300.workloads import WORKLOAD_OPTIONS
 
     cavs = [cavity(s.nx, s.ny, s.Re, s.n, theta_deg=s.theta_deg, U_lid=s.U_lid, L=s.L, H=s.H)
             for s in specs]
-    return Solver(cavs, stream=stream, precision=precision, kernel=kernel)
+    opts = dict(WORKLOAD_OPTIONS.get(workload, {}), **extra)
+    return Solver(cavs, stream=stream, precision=precision, kernel=kernel, **opts)
+
+
+def tuning_options(tuning):
+    names = {0: "grid", 1: "static", 2: "dynamic"}
+    return dict(fused_threads=tuning.fused_threads, fused_rows=tuning.fused_rows,
+                schedule=names[tuning.schedule])
+
+
+def one_by_one_mlups(specs, precision, kernel, workload, steps, tuning):
+    """The same cavities as separate handles, stepped one after another each
+    time step (one launch per cavity instead of one per batch)."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+
+    stream = torch.cuda.Stream()
+    extra = tuning_options(tuning) if tuning is not None else {}
+    solvers = [make_solver([sp], precision, kernel, stream=stream, workload=workload, **extra)
+               for sp in specs]
+    for s in solvers:
+        s.step(3)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for s in solvers:
+            capi.ifdlbm_step(s.h, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    for s in solvers:
+        s.close()
+    return sum(sp.nodes for sp in specs) * steps / (ms * 1e-3) / 1e6
 
 
 def reduce_over_ranks(total_ms, launches, world, device):
@@ -256,8 +291,11 @@ def run_ours(args):
     specs = WORKLOADS[args.workload]()
     lu_step = sum(s.nodes for s in specs)
 
-    s = make_solver(specs, args.precision, args.kernel)
+    s = make_solver(specs, args.precision, args.kernel, workload=args.workload)
     stream = s.stream
+    tuning = None
+    if capi.ifdlbm_info(s.h, 0).fused_threads:
+        tuning = s.autotune(trial_steps=10)           # layout and schedule, state unchanged
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(local)
     sampler.start()
@@ -317,7 +355,13 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, specs, stream, world)
+        e2e = run_e2e(args, specs, stream, world, tuning)
+    batch = None
+    if len(specs) > 1 and rank == 0:
+        batch = {"cavities": len(specs), "batched_mlups": None,
+                 "one_by_one_mlups": round(one_by_one_mlups(specs, args.precision, args.kernel,
+                                                            args.workload, max(5, args.steps // 4),
+                                                            tuning), 2)}
 
     out = None
     if rank == 0:
@@ -349,6 +393,14 @@ def run_ours(args):
             "e2e": e2e,
             "last_residual_cavity0": [float(x) for x in resid[0]],
         }
+        if tuning is not None:
+            out["config"]["autotuned"] = {"fused_threads": tuning.fused_threads,
+                                          "fused_rows": tuning.fused_rows,
+                                          "schedule": ["grid", "static", "dynamic"][tuning.schedule],
+                                          "tasks": tuning.ntasks, "candidates": tuning.candidates}
+        if batch is not None:
+            batch["batched_mlups"] = out["value"]
+            out["batch"] = batch
         if world == 1 and not args.no_adjoint:
             out["adjoint"] = run_adjoint_measure()
         if world == 1 and not args.no_cpu_baseline:
@@ -399,7 +451,7 @@ def run_adjoint_measure(nx=257, ny=257, T=2000, every=100, n=0.75, Re=400.0, the
             "J": float(J.detach())}
 
 
-def run_e2e(args, specs, stream, world):
+def run_e2e(args, specs, stream, world, tuning=None):
     """Same metric through the public API with HOST buffers: create the batch
     from host parameters, then every step reads its residual back into pinned
     host memory (a device -> host copy and a synchronisation per step), and
@@ -415,7 +467,8 @@ def run_e2e(args, specs, stream, world):
     fields = [torch.empty((4, sp.ny, sp.nx), dtype=torch.float64, pin_memory=True) for sp in specs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    s = make_solver(specs, args.precision, args.kernel, stream=stream)
+    extra = tuning_options(tuning) if tuning is not None else {}
+    s = make_solver(specs, args.precision, args.kernel, stream=stream, workload=args.workload, **extra)
     for _ in range(nsteps):
         capi.ifdlbm_step(s.h, 1)
         capi.ifdlbm_batch_residual(s.h, pinned.numpy())

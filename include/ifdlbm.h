@@ -75,7 +75,7 @@ typedef struct {
   double eta_b;     /* blend of Eq. (2.5) in [0, 1]; default 0.5 */
   double gamma_min; /* zero-shear clamp of |gamma-dot|; <= 0 means 1e-3 U/H;
                        otherwise >= 1e-100 */
-  double dt;        /* time step; <= 0 means cfl * min(L/(nx-1), H/(ny-1)) / c */
+  double dt;        /* time step; <= 0: derived from cfl by dt_mode */
   double rho0;      /* reference density, 1.0 */
   int precision;    /* IFDLBM_FP64 (default) or IFDLBM_FP32DEV */
   int kernel;       /* IFDLBM_KERNEL_*; default AUTO */
@@ -85,7 +85,35 @@ typedef struct {
                         only); each CTA owns at most fused_threads - 8
                         columns; 0 = 128 */
   int fused_rows;    /* FUSED: rows per CTA task (>= 2); 0 = automatic */
+  int schedule;      /* FUSED: IFDLBM_SCHED_*; default GRID */
+  int dt_mode;       /* IFDLBM_DT_*: how dt follows from cfl when dt <= 0 */
 } ifdlbm_options;
+
+/* Time-step rules ("c = 1, CFL = 0.5", Sec. 5.1). */
+#define IFDLBM_DT_GRID 0          /* dt = cfl * min(L/(nx-1), H/(ny-1)) / c (default) */
+#define IFDLBM_DT_CONTRAVARIANT 1 /* dt = cfl * min(dxi / max|c_xi|, deta / max|c_eta|),
+                                     the Courant number of the contravariant speeds
+                                     of Eq. (3.4); needed for theta < 45 deg */
+
+/* Cavity-to-CTA schedules of the fused kernel. Tasks are strips of columns x
+ * segments of rows of every cavity of the batch. */
+#define IFDLBM_SCHED_GRID 0    /* one CTA per task */
+#define IFDLBM_SCHED_STATIC 1  /* persistent CTAs (SMs x resident CTAs); CTA b takes
+                                  the positions b, b + grid, ... of the tasks
+                                  sorted largest first */
+#define IFDLBM_SCHED_DYNAMIC 2 /* persistent CTAs taking the next position of that
+                                  order from an atomic counter */
+
+/* Result of ifdlbm_autotune. */
+typedef struct {
+  int fused_threads;
+  int fused_rows;
+  int schedule;
+  int ntasks;
+  double ms_per_step; /* mean event time of the trial steps */
+  int candidates;     /* configurations timed */
+  int pad;
+} ifdlbm_tuning;
 
 /* One cavity of a batch (pattern "batching"). */
 typedef struct {
@@ -110,6 +138,7 @@ typedef struct {
   int64_t steps;      /* time steps taken so far */
   int64_t device_bytes; /* device memory owned by the whole handle */
   int64_t h2d_bytes;    /* bytes the handle copied host -> device at creation */
+  int fused_threads, fused_rows, schedule, ntasks; /* fused kernel layout in use */
 } ifdlbm_info_t;
 
 typedef struct ifdlbm_ctx *ifdlbm_handle;
@@ -263,6 +292,15 @@ int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *
 int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double *v1,
                                   const double *p1, const double *u0, const double *v0,
                                   const double *p0, double *out, void *stream);
+
+/* Autotuner of the batched fused step (pattern "batching"): times
+ * `trial_steps` >= 1 steps of every combination of fused_threads {64, 128,
+ * 256 (FP32DEV only)}, rows per task {16, 32, 64, 128} and schedule {GRID,
+ * STATIC, DYNAMIC} on the handle's own cavities, starting each trial from
+ * the same saved state, and keeps the fastest. The state is restored
+ * afterwards, so the call does not advance the simulation. Needs a handle
+ * using IFDLBM_KERNEL_FUSED. Synchronises; *best receives the choice. */
+int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best);
 
 /* Discrete adjoint (reverse mode) of the step, for gradients of a scalar
  * objective with respect to n, Re and theta (pattern "differentiation").

@@ -391,18 +391,26 @@ def periodic_grid(nx, ny, Lx=1.0, Ly=1.0, periodic_eta=True, c=1.0):
 
 
 def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None,
-                  gamma_min=None, dt=None):
+                  gamma_min=None, dt=None, dt_mode="grid", grid=None):
     """Parameters of a cavity run.
 
     * K from Re, Eq. (2.15.1).
     * READING (time step): dt = CFL * min(L dxi, H deta) / c, with the
-      paper's c = 1 and CFL = 0.5 (Sec. 5.1).
+      paper's c = 1 and CFL = 0.5 (Sec. 5.1) (dt_mode "grid"). With
+      dt_mode "contravariant" (and the cavity's Grid), the Courant number
+      applies to the contravariant speeds of Eq. (3.4):
+      dt = CFL * min(dxi / max|c_xi|, deta / max|c_eta|), taken over all
+      nodes and directions.
     * READING (blend): eta_b, which the paper leaves free in [0, 1], defaults
       to DEFAULT_ETA_B.
     * READING (zero-shear clamp): gamma_min defaults to 1e-3 U / H.
     """
     K = consistency_coefficient(Re, n, U, H)
-    if dt is None:
+    if dt is None and dt_mode == "contravariant":
+        mxi = float(np.max(np.abs(_re(grid.cxi))))
+        meta = float(np.max(np.abs(_re(grid.ceta))))
+        dt = cfl * min(grid.dxi / mxi, grid.deta / meta)
+    elif dt is None:
         dt = cfl * min(L / (nx - 1), H / (ny - 1)) / c
     if eta_b is None:
         eta_b = DEFAULT_ETA_B
@@ -668,6 +676,6 @@ def cavity_run(n_nodes, Re, n, theta_deg=60.0, U=0.1, L=1.0, H=1.0, ny=None, **k
     nx = n_nodes
     ny = n_nodes if ny is None else ny
     g = cavity_grid(nx, ny, L, H, theta_deg, U)
-    prm = cavity_params(nx, ny, Re, n, U=U, H=H, L=L, **kw)
+    prm = cavity_params(nx, ny, Re, n, U=U, H=H, L=L, grid=g, **kw)
     fhat, lam = initial_state(g, prm)
     return Run(g=g, prm=prm, fhat=fhat, lam=lam)

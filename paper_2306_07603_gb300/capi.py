@@ -34,6 +34,11 @@ IFDLBM_KPROF_REDUCE = 3
 IFDLBM_KPROF_FUSED = 4
 IFDLBM_KPROF_COUNT = 5
 IFDLBM_STATIC_MAX_NODES = 2097152
+IFDLBM_DT_GRID = 0
+IFDLBM_DT_CONTRAVARIANT = 1
+IFDLBM_SCHED_GRID = 0
+IFDLBM_SCHED_STATIC = 1
+IFDLBM_SCHED_DYNAMIC = 2
 
 
 class ifdlbm_geometry(C.Structure):
@@ -44,7 +49,8 @@ class ifdlbm_options(C.Structure):
     _fields_ = [("cfl", C.c_double), ("c", C.c_double), ("eta_b", C.c_double),
                 ("gamma_min", C.c_double), ("dt", C.c_double), ("rho0", C.c_double),
                 ("precision", C.c_int), ("kernel", C.c_int), ("graph_chunk", C.c_int),
-                ("fused_threads", C.c_int), ("fused_rows", C.c_int)]
+                ("fused_threads", C.c_int), ("fused_rows", C.c_int), ("schedule", C.c_int),
+                ("dt_mode", C.c_int)]
 
 
 class ifdlbm_cavity(C.Structure):
@@ -56,7 +62,15 @@ class ifdlbm_info_t(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("precision", C.c_int), ("kernel", C.c_int),
                 ("dt", C.c_double), ("K", C.c_double), ("gamma_min", C.c_double),
                 ("eta_b", C.c_double), ("courant_max", C.c_double), ("steps", C.c_int64),
-                ("device_bytes", C.c_int64), ("h2d_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("h2d_bytes", C.c_int64),
+                ("fused_threads", C.c_int), ("fused_rows", C.c_int), ("schedule", C.c_int),
+                ("ntasks", C.c_int)]
+
+
+class ifdlbm_tuning(C.Structure):
+    _fields_ = [("fused_threads", C.c_int), ("fused_rows", C.c_int), ("schedule", C.c_int),
+                ("ntasks", C.c_int), ("ms_per_step", C.c_double), ("candidates", C.c_int),
+                ("pad", C.c_int)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -92,6 +106,7 @@ _SIGS = {
                                                 C.c_void_p]),
     "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
+    "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
     "ifdlbm_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
@@ -269,6 +284,12 @@ def ifdlbm_residual_fields_static(nx, ny, u1, v1, p1, u0, v0, p0, out, stream=0)
     return _check(load_library().ifdlbm_residual_fields_static(
         int(nx), int(ny), _ptr(u1), _ptr(v1), _ptr(p1), _ptr(u0), _ptr(v0), _ptr(p0), _ptr(out),
         C.c_void_p(int(stream))))
+
+
+def ifdlbm_autotune(h, trial_steps=10) -> "ifdlbm_tuning":
+    best = ifdlbm_tuning()
+    _check(load_library().ifdlbm_autotune(h, int(trial_steps), C.byref(best)), h)
+    return best
 
 
 def ifdlbm_adjoint_seed_energy(h, state, adj, dparams):

@@ -43,7 +43,13 @@ struct ifdlbm_ctx {
   int ntiles = 0;
   int ntasks = 0;      // fused kernel tasks
   int fused_nt = 128;  // fused kernel threads per CTA
+  int fused_rows = 0;  // rows per task (0: automatic)
+  int schedule = IFDLBM_SCHED_GRID;
+  int grid = 0;        // CTAs per fused launch
+  int task_cap = 0;    // capacity of tasks / order / partial slots
   ifd::Task *tasks = nullptr;
+  int *order = nullptr;
+  int *counter = nullptr;
   // adjoint scratch (allocated on the first adjoint call)
   double *adj_g1 = nullptr, *adj_l1 = nullptr, *adj_fhb = nullptr, *adj_fbarb = nullptr,
          *adj_fbb = nullptr, *adj_lamb2 = nullptr, *adj_ppart = nullptr;
@@ -170,6 +176,10 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.cav = h->b.cav;
     f.geo = h->b.geo;
     f.tasks = h->tasks;
+    f.order = h->order;
+    f.counter = h->counter;
+    f.ntasks = h->ntasks;
+    f.schedule = h->schedule;
     f.g_in = h->b.g[parity];
     f.g_out = h->b.g[parity ^ 1];
     f.lam_in = h->b.lam[parity];
@@ -178,7 +188,8 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.status = h->b.status;
     f.powtab = h->b.powtab;
     f.want_residual = want_residual ? 1 : 0;
-    timed(h, IFDLBM_KPROF_FUSED, [&] { ifd::launch_fused<T>(f, h->fused_nt, h->ntasks, h->stream); });
+    if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
+    timed(h, IFDLBM_KPROF_FUSED, [&] { ifd::launch_fused<T>(f, h->fused_nt, h->grid, h->stream); });
     if (want_residual)
       timed(h, IFDLBM_KPROF_REDUCE, [&] {
         ifd::launch_residual_reduce(h->b.cav, h->b.part, h->b.resid, h->ncav, h->stream);
@@ -251,6 +262,71 @@ int check_status(ifdlbm_ctx *h) {
 
 bool cavity_ok(ifdlbm_ctx *h, int cavity) { return h && cavity >= 0 && cavity < h->ncav; }
 
+// (Re)builds the fused kernel's tasks: per cavity, balanced strips of at most
+// nt - 8 columns times balanced segments of about `rows` rows (0: automatic),
+// partial slots per cavity contiguous, and the scheduling order (largest
+// tasks first). Uploads the tasks, the order and the cavity table; drops
+// captured graphs. Asynchronous on the handle's stream.
+int build_fused_tasks(ifdlbm_ctx *h, int nt, int rows, int sched) {
+  const int W = nt - 8;
+  std::vector<ifd::Task> tasks;
+  for (int k = 0; k < h->ncav; ++k) {
+    CavDev &cv = h->cav[k];
+    const int hs = rows ? rows : (h->total_plane < (int64_t(8) << 20) ? 32 : 64);
+    const int sx = (cv.nx + W - 1) / W;
+    const int sy = std::max(1, std::min((cv.ny + hs - 1) / hs, cv.ny / 2));
+    cv.part0 = int(tasks.size());
+    for (int b = 0; b < sy; ++b)
+      for (int a = 0; a < sx; ++a) {
+        ifd::Task t{};
+        t.cav = k;
+        t.i0 = int(int64_t(a) * cv.nx / sx);
+        t.i1 = int(int64_t(a + 1) * cv.nx / sx);
+        t.j0 = int(int64_t(b) * cv.ny / sy);
+        t.j1 = int(int64_t(b + 1) * cv.ny / sy);
+        tasks.push_back(t);
+      }
+    cv.nparts = int(tasks.size()) - cv.part0;
+  }
+  if (int(tasks.size()) > h->task_cap)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "fused layout needs more tasks than allocated");
+  std::vector<int> order(tasks.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = int(i);
+  auto cost = [&](int i) {
+    const ifd::Task &t = tasks[i];
+    return int64_t(t.i1 - t.i0 + 8) * (t.j1 - t.j0 + 8);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost(a) > cost(b); });
+  const bool fp64 = h->precision == IFDLBM_FP64;
+  const int per_sm = fp64 ? ifd::fused_blocks_per_sm<double>(nt) : ifd::fused_blocks_per_sm<float>(nt);
+  if (per_sm < 1) return fail(h, IFDLBM_ERR_INVALID_ARG, "fused layout does not fit on an SM");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  h->ntasks = int(tasks.size());
+  h->fused_nt = nt;
+  h->fused_rows = rows;
+  h->schedule = sched;
+  h->grid = sched == IFDLBM_SCHED_GRID ? h->ntasks : std::min(h->ntasks, sms * per_sm);
+  for (int p = 0; p < 2; ++p)
+    if (h->gexec[p]) {
+      cudaGraphExecDestroy(h->gexec[p]);
+      h->gexec[p] = nullptr;
+    }
+  cudaError_t e = cudaMemcpyAsync(h->tasks, tasks.data(), tasks.size() * sizeof(ifd::Task),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->order, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.cav, h->cav.data(), h->cav.size() * sizeof(CavDev),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host vectors go out of scope
+  if (e != cudaSuccess) return cuda_fail(h, e, "fused tasks upload");
+  h->h2d_bytes += int64_t(tasks.size() * (sizeof(ifd::Task) + sizeof(int)) +
+                          h->cav.size() * sizeof(CavDev));
+  return IFDLBM_OK;
+}
+
 }  // namespace
 
 int ifd::set_global_error(int code, const std::string &msg) { return fail(nullptr, code, msg); }
@@ -293,6 +369,8 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   opt->graph_chunk = 32;
   opt->fused_threads = 0;
   opt->fused_rows = 0;
+  opt->schedule = IFDLBM_SCHED_GRID;
+  opt->dt_mode = IFDLBM_DT_GRID;
   return IFDLBM_OK;
 }
 
@@ -319,6 +397,10 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
         (opt.fused_threads == 256 && opt.precision == IFDLBM_FP32DEV)))
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
                 "options: fused_threads must be 0, 64, 128 or (FP32DEV) 256");
+  if (opt.dt_mode != IFDLBM_DT_GRID && opt.dt_mode != IFDLBM_DT_CONTRAVARIANT)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown dt_mode");
+  if (opt.schedule < IFDLBM_SCHED_GRID || opt.schedule > IFDLBM_SCHED_DYNAMIC)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown schedule");
   if (opt.fused_rows < 0 || opt.fused_rows == 1)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_rows must be 0 or >= 2");
   if (opt.graph_chunk < 0 || (opt.graph_chunk % 2) != 0)
@@ -387,6 +469,22 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     cv.nm1 = s.n - 1.0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
+    if (opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_CONTRAVARIANT) {
+      // CFL applied to the contravariant speeds of Eq. (3.4): their largest
+      // magnitudes sit at the ends of the xi range and at eta = 0 (x_xi smallest)
+      double mxi = 0.0;
+      for (int jj : {0, s.ny - 1})
+        for (int ii : {0, s.nx - 1})
+          for (int q = 1; q < 9; ++q) {
+            static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            const double eta = double(jj) / (s.ny - 1), xi = double(ii) / (s.nx - 1);
+            const double x_xi = L + 2.0 * H * ct * eta, x_eta = H * ct * (2.0 * xi - 1.0);
+            mxi = std::max(mxi, std::fabs(opt.c * (EX[q] - EY[q] * x_eta / H) / x_xi));
+          }
+      const double meta = opt.c / H;
+      cv.dt = opt.cfl * std::min((1.0 / (s.nx - 1)) / mxi, (1.0 / (s.ny - 1)) / meta);
+    }
     cv.eta_b = opt.eta_b;
     cv.dxi = 1.0 / (s.nx - 1);
     cv.deta = 1.0 / (s.ny - 1);
@@ -436,32 +534,13 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->ntiles = tile0;
   h->total_plane = off;
   h->geo_len = goff;
-  // fused tasks: balanced strips of at most fused_nt - 8 columns, balanced row segments
-  std::vector<ifd::Task> tasks;
-  if (fused) {
-    const int W = h->fused_nt - 8;
-    for (int k = 0; k < ncav; ++k) {
-      CavDev &cv = h->cav[k];
-      const int sx = (cv.nx + W - 1) / W;
-      // automatic segment height: shorter segments give more CTAs to small batches
-      const int hs = opt.fused_rows ? opt.fused_rows : (h->total_plane < (int64_t(8) << 20) ? 32 : 64);
-      const int sy = std::max(1, std::min((cv.ny + hs - 1) / hs, cv.ny / 2));
-      cv.part0 = int(tasks.size());
-      for (int b = 0; b < sy; ++b)
-        for (int a = 0; a < sx; ++a) {
-          ifd::Task t{};
-          t.cav = k;
-          t.i0 = int(int64_t(a) * cv.nx / sx);
-          t.i1 = int(int64_t(a + 1) * cv.nx / sx);
-          t.j0 = int(int64_t(b) * cv.ny / sy);
-          t.j1 = int(int64_t(b + 1) * cv.ny / sy);
-          tasks.push_back(t);
-        }
-      cv.nparts = int(tasks.size()) - cv.part0;
-    }
-    h->ntasks = int(tasks.size());
+  if (fused) {  // task capacity: the finest layout the autotuner tries (64 threads, 16 rows)
+    int cap = 0;
+    const int rmin = opt.fused_rows ? std::min(opt.fused_rows, 16) : 16;
+    for (const CavDev &cv : h->cav)
+      cap += ((cv.nx + 55) / 56) * std::max(1, std::min((cv.ny + rmin - 1) / rmin, cv.ny / 2));
+    h->task_cap = std::max(cap, 1);
   }
-
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
   bool ok = true;
   for (int p = 0; p < 2; ++p) {
@@ -474,9 +553,11 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     ok &= (h->b.fh = A(9 * off * tsize)) != nullptr;
     ok &= (h->b.m0 = (double *)A(3 * off * sizeof(double))) != nullptr;
   } else {
-    ok &= (h->tasks = (ifd::Task *)A(tasks.size() * sizeof(ifd::Task))) != nullptr;
+    ok &= (h->tasks = (ifd::Task *)A(size_t(h->task_cap) * sizeof(ifd::Task))) != nullptr;
+    ok &= (h->order = (int *)A(size_t(h->task_cap) * sizeof(int))) != nullptr;
+    ok &= (h->counter = (int *)A(sizeof(int))) != nullptr;
   }
-  const int nslots = fused ? h->ntasks : h->ntiles;
+  const int nslots = fused ? h->task_cap : h->ntiles;
   ok &= (h->b.part = (double *)A(size_t(nslots) * ifd::NPART * sizeof(double))) != nullptr;
   ok &= (h->b.resid = (double *)A(size_t(ncav) * 4 * sizeof(double))) != nullptr;
   ok &= (h->b.tile_cav = (int *)A(size_t(h->ntiles) * sizeof(int))) != nullptr;
@@ -510,7 +591,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
 
   std::vector<int> tile_cav(h->ntiles);
   for (int k = 0; k < ncav; ++k)
-    for (int t = 0; t < h->cav[k].nparts; ++t) tile_cav[h->cav[k].tile0 + t] = k;
+    for (int t = 0; t < h->cav[k].tiles_x * h->cav[k].tiles_y; ++t) tile_cav[h->cav[k].tile0 + t] = k;
   std::vector<double> geo_h(4 * goff);
   std::copy(xix.begin(), xix.end(), geo_h.begin());
   std::copy(xeH.begin(), xeH.end(), geo_h.begin() + goff);
@@ -544,9 +625,14 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     if (ptr && e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, 9 * off * tsize, s);
   if (h->b.m0 && e == cudaSuccess) e = cudaMemsetAsync(h->b.m0, 0, 3 * off * sizeof(double), s);
   if (fused && e == cudaSuccess) {
-    e = cudaMemcpyAsync(h->tasks, tasks.data(), tasks.size() * sizeof(ifd::Task),
-                        cudaMemcpyHostToDevice, s);
-    h->h2d_bytes += int64_t(tasks.size() * sizeof(ifd::Task));
+    int rc = build_fused_tasks(h, h->fused_nt, opt.fused_rows, opt.schedule);
+    if (rc) {
+      std::string msg = h->err;
+      release_all(h);
+      delete h;
+      return fail(nullptr, rc, msg);
+    }
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
@@ -767,6 +853,10 @@ int ifdlbm_info(ifdlbm_handle h, int cavity, ifdlbm_info_t *info) {
   info->steps = h->steps;
   info->device_bytes = h->bytes;
   info->h2d_bytes = h->h2d_bytes;
+  info->fused_threads = h->kernel == IFDLBM_KERNEL_FUSED ? h->fused_nt : 0;
+  info->fused_rows = h->fused_rows;
+  info->schedule = h->schedule;
+  info->ntasks = h->ntasks;
   return IFDLBM_OK;
 }
 
@@ -879,6 +969,64 @@ int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step");
   return IFDLBM_OK;
+}
+
+int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best) {
+  if (!h || !best || trial_steps < 1) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  if (h->kernel != IFDLBM_KERNEL_FUSED)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "autotune: needs a handle using the fused kernel");
+  cudaSetDevice(h->device);
+  const int64_t nbytes = ifdlbm_state_bytes(h);
+  void *saved = dalloc(h, size_t(nbytes));
+  if (!saved) return fail(h, IFDLBM_ERR_OOM, "autotune: device allocation failed");
+  int rc = ifdlbm_save_state_dev(h, saved);
+  if (rc) return rc;
+  const bool profiling = h->profiling;
+  h->profiling = false;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  ifdlbm_tuning b{};
+  b.ms_per_step = 1e300;
+  const int nts[3] = {64, 128, 256};
+  const int rows[4] = {16, 32, 64, 128};
+  for (int nt : nts) {
+    if (nt == 256 && h->precision == IFDLBM_FP64) continue;
+    for (int r : rows)
+      for (int sc = IFDLBM_SCHED_GRID; sc <= IFDLBM_SCHED_DYNAMIC; ++sc) {
+        if ((rc = build_fused_tasks(h, nt, r, sc))) goto done;
+        if ((rc = ifdlbm_load_state_dev(h, saved))) goto done;
+        for (int w = 0; w < 2; ++w) enqueue_step_any(h, h->cur ^ (w & 1), false);
+        cudaEventRecord(e0, h->stream);
+        for (int st = 0; st < trial_steps; ++st) enqueue_step_any(h, h->cur ^ (st & 1), false);
+        cudaEventRecord(e1, h->stream);
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+          rc = cuda_fail(h, e, "autotune trial");
+          goto done;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        g_launches += int64_t(trial_steps + 2) * launches_per_step(h, false);
+        ++b.candidates;
+        if (ms / trial_steps < b.ms_per_step) {
+          b.ms_per_step = ms / trial_steps;
+          b.fused_threads = nt;
+          b.fused_rows = r;
+          b.schedule = sc;
+        }
+      }
+  }
+  rc = build_fused_tasks(h, b.fused_threads, b.fused_rows, b.schedule);
+  if (!rc) rc = ifdlbm_load_state_dev(h, saved);
+  if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = fail(h, IFDLBM_ERR_CUDA, "autotune");
+  b.ntasks = h->ntasks;
+  *best = b;
+done:
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->profiling = profiling;
+  return rc;
 }
 
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,

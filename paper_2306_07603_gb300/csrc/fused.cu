@@ -119,11 +119,8 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 }  // namespace
 
 template <class T, int NT>
-__global__ void __launch_bounds__(NT) k_fused(FusedArgs a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
-
-  const Task task = a.tasks[blockIdx.x];
+__device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
+  const Task task = a.tasks[ti];
   const CavDev &cv = a.cav[task.cav];
   const int i0 = task.i0, i1 = task.i1, j0 = task.j0, j1 = task.j1;
   const int nx = cv.nx, ny = cv.ny;
@@ -351,19 +348,73 @@ __global__ void __launch_bounds__(NT) k_fused(FusedArgs a) {
     leaf_flush(leaf, p);
     p.du2max = double(leaf.du2max);
     p.u2max = double(leaf.u2max);
-    block_partial<NT / 32>(p, a.part, blockIdx.x);
+    block_partial<NT / 32>(p, a.part, ti);
+  }
+  __syncthreads();  // the next task reuses the shared rings
+}
+
+// Schedules: 0 one CTA per task; 1 persistent CTAs taking positions
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the largest-first order;
+// 2 persistent CTAs taking positions from an atomic counter (no waiting on
+// other CTAs: a CTA that finds the list exhausted returns).
+template <class T, int NT>
+__global__ void __launch_bounds__(NT) k_fused(FusedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
+  __shared__ int next;
+  if (a.schedule == 0) {
+    fused_task<T, NT>(a, S, blockIdx.x);
+    return;
+  }
+  for (int it = 0;; ++it) {
+    int pos;
+    if (a.schedule == 1) {
+      pos = blockIdx.x + it * gridDim.x;
+    } else {
+      if (threadIdx.x == 0) next = atomicAdd(a.counter, 1);
+      __syncthreads();
+      pos = next;
+      __syncthreads();
+    }
+    if (pos >= a.ntasks) return;
+    fused_task<T, NT>(a, S, a.order[pos]);
   }
 }
 
 template <class T, int NT>
-static void launch_fused_nt(const FusedArgs &a, int ntasks, cudaStream_t s) {
-  const int smem = int(sizeof(FusedSmem<T, NT>));
+static void configure_nt() {
   static bool configured = false;  // the attribute is per function
   if (!configured) {
-    cudaFuncSetAttribute(k_fused<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_fused<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(sizeof(FusedSmem<T, NT>)));
     configured = true;
   }
-  k_fused<T, NT><<<ntasks, NT, smem, s>>>(a);
+}
+
+template <class T, int NT>
+static void launch_fused_nt(const FusedArgs &a, int grid, cudaStream_t s) {
+  configure_nt<T, NT>();
+  k_fused<T, NT><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+}
+
+template <class T, int NT>
+static int blocks_per_sm_nt() {
+  configure_nt<T, NT>();
+  int n = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT>, NT,
+                                                int(sizeof(FusedSmem<T, NT>)));
+  return n;
+}
+
+template <class T> int fused_blocks_per_sm(int nt) {
+  switch (nt) {
+    case 64: return blocks_per_sm_nt<T, 64>();
+    case 128: return blocks_per_sm_nt<T, 128>();
+    case 256:
+      if constexpr (sizeof(T) == 4) return blocks_per_sm_nt<T, 256>();
+      return 0;
+  }
+  return 0;
 }
 
 template <class T> int fused_smem_bytes(int nt) {
@@ -393,5 +444,7 @@ template bool launch_fused<float>(const FusedArgs &, int, int, cudaStream_t);
 template bool launch_fused<double>(const FusedArgs &, int, int, cudaStream_t);
 template int fused_smem_bytes<float>(int);
 template int fused_smem_bytes<double>(int);
+template int fused_blocks_per_sm<float>(int);
+template int fused_blocks_per_sm<double>(int);
 
 }  // namespace ifd

@@ -87,6 +87,10 @@ struct FusedArgs {
   const CavDev *cav;
   Geo geo;
   const Task *tasks;
+  const int *order;   // scheduled position -> task index (largest tasks first)
+  int *counter;       // dynamic schedule: next position (zeroed before each launch)
+  int ntasks;
+  int schedule;       // 0 grid (one CTA per task), 1 persistent static, 2 persistent dynamic
   const void *g_in;
   void *g_out;
   const double *lam_in;
@@ -100,6 +104,7 @@ struct FusedArgs {
 // Fused kernel (fused.cu); nt in {64, 128, 256} (256 in FP32 only).
 template <class T> bool launch_fused(const FusedArgs &a, int nt, int ntasks, cudaStream_t s);
 template <class T> int fused_smem_bytes(int nt);
+template <class T> int fused_blocks_per_sm(int nt);
 
 // Staged kernels (staged.cu)
 template <class T> void launch_collide(const StepArgs &a, int ntiles, cudaStream_t s);

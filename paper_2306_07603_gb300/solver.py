@@ -13,10 +13,13 @@ from . import capi
 _PREC = {"fp64": capi.IFDLBM_FP64, "fp32dev": capi.IFDLBM_FP32DEV}
 _KERN = {"auto": capi.IFDLBM_KERNEL_AUTO, "staged": capi.IFDLBM_KERNEL_STAGED,
          "fused": capi.IFDLBM_KERNEL_FUSED}
+_SCHED = {"grid": capi.IFDLBM_SCHED_GRID, "static": capi.IFDLBM_SCHED_STATIC,
+          "dynamic": capi.IFDLBM_SCHED_DYNAMIC}
 
 
 def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, dt=None,
-                 gamma_min=None, graph_chunk=None, fused_threads=None, fused_rows=None):
+                 gamma_min=None, graph_chunk=None, fused_threads=None, fused_rows=None,
+                 schedule=None, dt_mode=None):
     opt = capi.ifdlbm_default_options()
     opt.precision = _PREC[precision]
     opt.kernel = _KERN[kernel]
@@ -25,6 +28,11 @@ def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, 
                       ("fused_threads", fused_threads), ("fused_rows", fused_rows)):
         if val is not None:
             setattr(opt, name, val)
+    if schedule is not None:
+        opt.schedule = _SCHED[schedule] if isinstance(schedule, str) else int(schedule)
+    if dt_mode is not None:
+        opt.dt_mode = {"grid": capi.IFDLBM_DT_GRID,
+                       "contravariant": capi.IFDLBM_DT_CONTRAVARIANT}[dt_mode]
     return opt
 
 
@@ -79,6 +87,10 @@ class Solver:
 
     def info(self, cavity=0):
         return capi.ifdlbm_info(self.h, cavity)
+
+    def autotune(self, trial_steps=10):
+        """Pick the fused kernel's CTA width, rows per task and schedule (state unchanged)."""
+        return capi.ifdlbm_autotune(self.h, trial_steps)
 
     def sync(self):
         capi.ifdlbm_sync(self.h)

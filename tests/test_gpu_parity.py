@@ -227,3 +227,73 @@ def test_divergence_is_reported_not_hidden():
     with pytest.raises(capi.IfdlbmError) as e:
         s.residual()
     assert e.value.code == capi.IFDLBM_ERR_DIVERGED
+
+
+@pytest.mark.parametrize("schedule", ["grid", "static", "dynamic"])
+def test_fused_schedules_match_oracle_on_uneven_batch(schedule):
+    """Persistent schedules (static largest-first, dynamic atomic counter) give
+    every cavity of an uneven batch the oracle's step (FP64 fused kernel)."""
+    specs = [(67, 45, 100.0, 0.75, 60.0), (33, 29, 1000.0, 0.5, 45.0), (41, 57, 400.0, 1.5, 75.0),
+             (9, 70, 100.0, 1.0, 90.0), (70, 9, 100.0, 1.25, 30.0)]
+    s = solver([cav(*sp) for sp in specs], kernel="fused", fused_threads=64, fused_rows=16,
+               schedule=schedule)
+    runs = []
+    for k, sp in enumerate(specs):
+        r = oracle_run(*sp)
+        r.advance(12)
+        s.set_state(k, r.fhat, r.lam)
+        runs.append(r)
+    s.step(3)
+    for k, r in enumerate(runs):
+        r.advance(2)
+        f_in, l_in = r.fhat.copy(), r.lam.copy()
+        r.advance(1)
+        fg, lg = s.get_state(k)
+        compare_state(fg, lg, r.fhat, r.lam, lam_tol=lam_bound(f_in, l_in, r.prm, r.lam))
+
+
+def test_autotune_keeps_state_and_result():
+    """The autotuner times layouts from a saved state and restores it: the
+    state is unchanged and later steps still equal the oracle's."""
+    specs = [(67, 45, 100.0, 0.75, 60.0), (41, 57, 400.0, 1.5, 75.0)]
+    s = solver([cav(*sp) for sp in specs], kernel="fused")
+    runs = []
+    for k, sp in enumerate(specs):
+        r = oracle_run(*sp)
+        r.advance(10)
+        s.set_state(k, r.fhat, r.lam)
+        runs.append(r)
+    before = [s.get_state(k) for k in range(2)]
+    t = s.autotune(trial_steps=2)
+    assert t.candidates == 24 and t.fused_threads in (64, 128) and t.schedule in (0, 1, 2)
+    info = s.info(0)
+    assert (info.fused_threads, info.fused_rows, info.schedule) == (t.fused_threads, t.fused_rows,
+                                                                     t.schedule)
+    for k in range(2):
+        f, l = s.get_state(k)
+        assert np.array_equal(f, before[k][0]) and np.array_equal(l, before[k][1])
+    s.step(2)
+    for k, r in enumerate(runs):
+        r.advance(1)
+        f_in, l_in = r.fhat.copy(), r.lam.copy()
+        r.advance(1)
+        fg, lg = s.get_state(k)
+        compare_state(fg, lg, r.fhat, r.lam, lam_tol=lam_bound(f_in, l_in, r.prm, r.lam))
+
+
+@pytest.mark.parametrize("kname", ["staged", "fused64x8"])
+def test_contravariant_time_step_theta30(kname):
+    """dt_mode 'contravariant' (dt = CFL min(dxi/max|c_xi|, deta/max|c_eta|)) gives
+    the oracle's dt and step at theta = 30 deg, where the default rule is unstable."""
+    from paper_2306_07603_gb300 import capi
+    nx, ny = 41, 37
+    run = O.cavity_run(nx, 400.0, 0.75, theta_deg=30.0, ny=ny, dt_mode="contravariant")
+    s = solver([cav(nx, ny, 400.0, 0.75, 30.0)], dt_mode="contravariant", **KERNELS[kname])
+    assert abs(capi.ifdlbm_info(s.h, 0).dt - run.prm.dt) <= 1e-15 * run.prm.dt
+    run.advance(30)
+    f0, l0 = run.fhat.copy(), run.lam.copy()
+    s.set_state(0, f0, l0)
+    s.step(1)
+    fo, lo = O.step(f0, l0, run.g, run.prm)
+    fg, lg = s.get_state(0)
+    compare_state(fg, lg, fo, lo, lam_tol=lam_bound(f0, l0, run.prm, lo))
