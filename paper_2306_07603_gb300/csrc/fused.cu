@@ -34,16 +34,16 @@ namespace ifd {
 
 namespace {
 
-constexpr int STAGE_ROWS = 4;  // depth of the cp.async prefetch ring
+constexpr int STAGE_ROWS = 3;  // depth of the cp.async prefetch ring (2 rows ahead)
 
+// Shared state per column thread: ~700 B in FP32, so that five 64-thread
+// CTAs fit on an SM.
 template <class T, int NT>
 struct FusedSmem {
   T st_g[STAGE_ROWS][9][NT];      // prefetched state g(t) of rows ahead
-  double st_l[STAGE_ROWS][NT];    // prefetched lambda_prev
   T fb[5][9][NT];                 // f-bar^+
   T fh[5][9][NT];                 // f(t + dt/2)
-  T fp[5][9][NT];                 // f-hat^+
-  T up[5][3][NT];                 // u, v, P at t (residual)
+  T fp[5][9][NT];                 // f-hat^+ (its moments are u, P at t: Eqs. 2.10-2.11)
   T lam[5][NT];                   // lambda(t)
   T gn[9][NT];                    // f-hat(t + dt) of the current stage-2 row
 };
@@ -79,6 +79,66 @@ template <int N>
 __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
+
+// Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side known
+// at compile time (eta direction: the side is the sign of e_iy, since
+// c_{i eta} = c e_iy / H); `edge` selects the first-order near-wall form.
+template <bool POS, class T>
+__device__ __forceinline__ T dmix2_side(T fm2, T fm1, T f0, T fp1, T fp2, bool edge, T eta_b) {
+  T up;
+  if (POS)
+    up = edge ? T(2) * (f0 - fm1) : (T(3) * f0 - T(4) * fm1 + fm2);
+  else
+    up = edge ? T(2) * (fp1 - f0) : -(T(3) * f0 - T(4) * fp1 + fp2);
+  return eta_b * (fp1 - fm1) + (T(1) - eta_b) * up;
+}
+
+// The same with the side chosen at run time (xi direction): the upwind
+// operands are selected, then one stencil is evaluated.
+template <class T>
+__device__ __forceinline__ T dmix2_sel(T fm2, T fm1, T f0, T fp1, T fp2, bool pos, bool edge_pos,
+                                       bool edge_neg, T eta_b) {
+  const T fa = pos ? fm1 : fp1, fb = pos ? fm2 : fp2;
+  const bool edge = pos ? edge_pos : edge_neg;
+  const T u = edge ? T(2) * (f0 - fa) : (T(3) * f0 - T(4) * fa + fb);
+  return eta_b * (fp1 - fm1) + (T(1) - eta_b) * (pos ? u : -u);
+}
+
+// c_{q xi} D_xi F + c_{q eta} D_eta F at an interior node: `row` is the xi
+// row of plane q (this thread at index t), `col` the five eta neighbours.
+template <int Q, class T>
+__device__ __forceinline__ T advect_q(const T *row, int t, const T col[5], T A, T B, T ceta_unit,
+                                      bool clo, bool chi, bool lo, bool hi, T eta_b, T i2dxi,
+                                      T i2deta) {
+  const T cxi = T(ex(Q)) * A - T(ey(Q)) * B;
+  const T f0 = col[2];
+  T adv = cxi * dmix2_sel(row[t - 2], row[t - 1], f0, row[t + 1], row[t + 2], cxi >= T(0), clo,
+                          chi, eta_b) * i2dxi;
+  if constexpr (ey(Q) != 0) {
+    const T ceta = T(ey(Q)) * ceta_unit;
+    const T dy = (ey(Q) > 0) ? dmix2_side<true>(col[0], col[1], f0, col[3], col[4], lo, eta_b)
+                             : dmix2_side<false>(col[0], col[1], f0, col[3], col[4], hi, eta_b);
+    adv += ceta * dy * i2deta;
+  }
+  return adv;
+}
+
+template <class T, int Q, int NT>
+struct AdvectAll {
+  // fills out[q] = F_q - scale * advection_q for q = Q..8
+  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int t, T A, T B,
+                                             T ceta_unit, bool clo, bool chi, bool lo, bool hi,
+                                             T eta_b, T i2dxi, T i2deta, T scale, const T *base,
+                                             T out[9]) {
+    const T col[5] = {cols[0][Q * NT], cols[1][Q * NT], cols[2][Q * NT], cols[3][Q * NT],
+                      cols[4][Q * NT]};
+    out[Q] = base[Q * NT] - scale * advect_q<Q>(rows + Q * NT, t, col, A, B, ceta_unit, clo, chi,
+                                                lo, hi, eta_b, i2dxi, i2deta);
+    if constexpr (Q < 8)
+      AdvectAll<T, Q + 1, NT>::run(rows, cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b, i2dxi,
+                                   i2deta, scale, base, out);
+  }
+};
 
 // Residual terms of one node, summed over up to 8 rows in T before they are
 // added to the FP64 partials (a leaf sum; every sum beyond it is FP64).
@@ -160,34 +220,59 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const int64_t node = int64_t(r) * cv.pitch + cc;
 #pragma unroll
       for (int q = 0; q < 9; ++q) cp_async(&S.st_g[s][q][t], gin + q * cv.plane + node, sizeof(T));
-      cp_async(&S.st_l[s][t], lam_in + node, 8);
     }
     cp_commit();
   };
+  // lambda_prev of the row Step (2) works on next, loaded one row ahead
+  auto lam_load = [&](int r) {
+    return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * cv.pitch + cc] : 0.0;
+  };
+  // per-cavity constants of the relaxation time, converted once
+  const double gmin2 = cv.gmin2, half_nm1 = cv.half_nm1, Kics2 = cv.Kics2;
+  const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
   // Step (2) for row r from the staging ring: moments, f^eq and lambda(t).
   // lambda of row k + 1 is formed during the full step of row k, so that the
   // FP64 power overlaps FP32 work instead of delaying the row it belongs to.
   T nux = 0, nuy = 0, nP = 0, ngeq[9];
   double nlam = 0.0;
-  auto collide_row = [&](int r) {
-    const int s = r % STAGE_ROWS;
+  struct Collided {
+    T ux, uy, P, geq[9];
+    double lam;
+  };
+  auto collide = [&](int r, double lam_prev) {
+    Collided o;
+    const int s = (r + STAGE_ROWS) % STAGE_ROWS;
     T g[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) g[q] = S.st_g[s][q][t];
-    const double lam_prev = S.st_l[s][t];
-    moments(g, c_, cs2, nux, nuy, nP);               // Eqs. (2.10)-(2.11)
-    equilibrium(nP, nux, nuy, c_, ics2, ngeq);       // Eq. (2.8)
+    moments(g, c_, cs2, o.ux, o.uy, o.P);                 // Eqs. (2.10)-(2.11)
+    equilibrium(o.P, o.ux, o.uy, c_, ics2, o.geq);        // Eq. (2.8)
     T d[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) d[q] = g[q] - ngeq[q];
+    for (int q = 0; q < 9; ++q) d[q] = g[q] - o.geq[q];
     T pxx, pxy, pyy;
     second_moments(d, c_, pxx, pxy, pyy);
-    nlam = relaxation_time(pxx, pxy, pyy, lam_prev, cv, a.powtab);  // Eqs. (1.4), (2.12)-(2.14)
+    // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as relaxation_time)
+    const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
+    const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
+    double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+    q = q > gmin2 ? q : gmin2;
+    o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
+    return o;
+  };
+  auto take = [&](const Collided &o) {
+    nux = o.ux;
+    nuy = o.uy;
+    nP = o.P;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ngeq[q] = o.geq[q];
+    nlam = o.lam;
   };
 #pragma unroll
   for (int r = 0; r < STAGE_ROWS - 1; ++r) prefetch(kb + r);
   cp_wait<STAGE_ROWS - 2>();
-  if (kb >= 0 && kb < ny) collide_row(kb);
+  if (kb >= 0 && kb < ny) take(collide(kb, lam_load(kb)));
+  double lp_next = lam_load(kb + 1);  // lambda_prev of row k + 1
 
   for (int k = kb; k <= ke; ++k) {
     prefetch(k + STAGE_ROWS - 1);
@@ -209,9 +294,6 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         S.fp[sA][q][t] = ap * gq + bp * ngeq[q];
       }
       S.lam[sA][t] = L;
-      S.up[sA][0][t] = nux;
-      S.up[sA][1][t] = nuy;
-      S.up[sA][2][t] = nP;
       if (k == 0) {
         u0s = nux;
         v0s = nuy;
@@ -232,17 +314,11 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const bool lo = m == 1, hi = m == ny - 2;
       T fbar[9];
       fbar[0] = S.fb[sm][0][t];
-#pragma unroll
-      for (int q = 1; q < 9; ++q) {
-        const T cxi = T(ex(q)) * A - T(ey(q)) * B;
-        const T ceta = T(ey(q)) * ceta_unit;
-        const T *row = S.fb[sm][q];
-        const T f0 = row[t];
-        const T dx = dmix2(row[t - 2], row[t - 1], f0, row[t + 1], row[t + 2], cxi >= T(0), clo,
-                           chi, eta_b) * i2dxi;
-        const T dy = dmix2(S.fb[sm2][q][t], S.fb[sm1][q][t], f0, S.fb[sp1][q][t], S.fb[sp2][q][t],
-                           ceta >= T(0), lo, hi, eta_b) * i2deta;
-        fbar[q] = f0 - hdt * (cxi * dx + ceta * dy);                  // Eq. (3.7)
+      {
+        const T *cols[5] = {&S.fb[sm2][0][t], &S.fb[sm1][0][t], &S.fb[sm][0][t], &S.fb[sp1][0][t],
+                            &S.fb[sp2][0][t]};
+        AdvectAll<T, 1, NT>::run(&S.fb[sm][0][0], cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
+                                 i2dxi, i2deta, hdt, &S.fb[sm][0][t], fbar);   // Eq. (3.7)
       }
       T ux, uy, P;
       moments(fbar, c_, cs2, ux, uy, P);
@@ -287,21 +363,19 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const T A = row_cxix<T>(a.geo, cv, o);
       const T B = A * xeH;
       const bool lo = o == 1, hi = o == ny - 2;
-      S.gn[0][t] = S.fp[so][0][t];
-#pragma unroll
-      for (int q = 1; q < 9; ++q) {
-        const T cxi = T(ex(q)) * A - T(ey(q)) * B;
-        const T ceta = T(ey(q)) * ceta_unit;
-        const T *row = S.fh[so][q];
-        const T f0 = row[t];
-        const T dx = dmix2(row[t - 2], row[t - 1], f0, row[t + 1], row[t + 2], cxi >= T(0), clo,
-                           chi, eta_b) * i2dxi;
-        const T dy = dmix2(S.fh[so2][q][t], S.fh[so1][q][t], f0, S.fh[sp1][q][t], S.fh[sp2][q][t],
-                           ceta >= T(0), lo, hi, eta_b) * i2deta;
-        S.gn[q][t] = S.fp[so][q][t] - dt * (cxi * dx + ceta * dy);    // Eq. (3.6)
+      T gnv[9];
+      gnv[0] = S.fp[so][0][t];
+      {
+        const T *cols[5] = {&S.fh[so2][0][t], &S.fh[so1][0][t], &S.fh[so][0][t], &S.fh[sp1][0][t],
+                            &S.fh[sp2][0][t]};
+        AdvectAll<T, 1, NT>::run(&S.fh[so][0][0], cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
+                                 i2dxi, i2deta, dt, &S.fp[so][0][t], gnv);     // Eq. (3.6)
       }
+#pragma unroll
+      for (int q = 0; q < 9; ++q) S.gn[q][t] = gnv[q];
     }
-    if (k + 1 <= rhi && k + 1 >= 0) collide_row(k + 1);  // lambda of the next row
+    if (k + 1 <= rhi && k + 1 >= 0) take(collide(k + 1, lp_next));  // lambda of the next row
+    lp_next = lam_load(k + 2);
     __syncthreads();
     if (do2 && own) {
       const int so = slot5(o);
@@ -313,10 +387,14 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 #pragma unroll
       for (int q = 0; q < 9; ++q) gout[q * cv.plane + node] = gnv[q];
       if (a.want_residual) {
-        T ux, uy, P;
+        T ux, uy, P, u0, v0, P0;
         moments(gnv, c_, cs2, ux, uy, P);
-        const T wJ = wx * T(cv.deta) * row_jac<T>(a.geo, cv, o);
-        leaf_add(leaf, p, ux, uy, P, S.up[so][0][t], S.up[so][1][t], S.up[so][2][t], wJ, a.status);
+        T fpo[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) fpo[q] = S.fp[so][q][t];
+        moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
+        const T wJ = wx * wy_in * row_jac<T>(a.geo, cv, o);
+        leaf_add(leaf, p, ux, uy, P, u0, v0, P0, wJ, a.status);
       }
       // wall rows produced with their neighbour rows
       const bool bottom = o == 1 && j0 == 0;
@@ -333,11 +411,14 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         if (a.want_residual) {
           T wx2, wy2, wP2;
           moments(F, c_, cs2, wx2, wy2, wP2);
-          const int sr = slot5(r);
-          const T ou = bottom ? u0s : S.up[sr][0][t];
-          const T ov = bottom ? v0s : S.up[sr][1][t];
-          const T oP = bottom ? P0s : S.up[sr][2][t];
-          const T wJ = wx * T(0.5 * cv.deta) * row_jac<T>(a.geo, cv, r);
+          T ou = u0s, ov = v0s, oP = P0s;
+          if (!bottom) {
+            T fpr[9];
+#pragma unroll
+            for (int q = 0; q < 9; ++q) fpr[q] = S.fp[slot5(r)][q][t];
+            moments(fpr, c_, cs2, ou, ov, oP);
+          }
+          const T wJ = wx * wy_edge * row_jac<T>(a.geo, cv, r);
           leaf_add(leaf, p, wx2, wy2, wP2, ou, ov, oP, wJ, a.status);
         }
       }
