@@ -81,8 +81,8 @@ typedef struct {
   int kernel;       /* IFDLBM_KERNEL_*; default AUTO */
   int graph_chunk;  /* steps per captured CUDA graph, even, >= 2; default 32;
                        0 disables graph capture */
-  int fused_threads; /* FUSED: threads per CTA, 64, 128 or 256 (256: FP32DEV
-                        only); each CTA owns at most fused_threads - 8
+  int fused_threads; /* FUSED: threads per CTA, 64, 128 or 256, two per
+                        column; each CTA owns at most fused_threads/2 - 8
                         columns; 0 = 128 */
   int fused_rows;    /* FUSED: rows per CTA task (>= 2); 0 = automatic */
   int schedule;      /* FUSED: IFDLBM_SCHED_*; default GRID */

@@ -263,12 +263,12 @@ int check_status(ifdlbm_ctx *h) {
 bool cavity_ok(ifdlbm_ctx *h, int cavity) { return h && cavity >= 0 && cavity < h->ncav; }
 
 // (Re)builds the fused kernel's tasks: per cavity, balanced strips of at most
-// nt - 8 columns times balanced segments of about `rows` rows (0: automatic),
+// nt/2 - 8 columns times balanced segments of about `rows` rows (0: automatic),
 // partial slots per cavity contiguous, and the scheduling order (largest
 // tasks first). Uploads the tasks, the order and the cavity table; drops
 // captured graphs. Asynchronous on the handle's stream.
 int build_fused_tasks(ifdlbm_ctx *h, int nt, int rows, int sched) {
-  const int W = nt - 8;
+  const int W = ifd::fused_strip_width(nt);
   std::vector<ifd::Task> tasks;
   for (int k = 0; k < h->ncav; ++k) {
     CavDev &cv = h->cav[k];
@@ -394,9 +394,8 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   if (opt.kernel < IFDLBM_KERNEL_AUTO || opt.kernel > IFDLBM_KERNEL_FUSED)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown kernel");
   if (!(opt.fused_threads == 0 || opt.fused_threads == 64 || opt.fused_threads == 128 ||
-        (opt.fused_threads == 256 && opt.precision == IFDLBM_FP32DEV)))
-    return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
-                "options: fused_threads must be 0, 64, 128 or (FP32DEV) 256");
+        opt.fused_threads == 256))
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_threads must be 0, 64, 128 or 256");
   if (opt.dt_mode != IFDLBM_DT_GRID && opt.dt_mode != IFDLBM_DT_CONTRAVARIANT)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown dt_mode");
   if (opt.schedule < IFDLBM_SCHED_GRID || opt.schedule > IFDLBM_SCHED_DYNAMIC)
@@ -537,8 +536,10 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   if (fused) {  // task capacity: the finest layout the autotuner tries (64 threads, 16 rows)
     int cap = 0;
     const int rmin = opt.fused_rows ? std::min(opt.fused_rows, 16) : 16;
+    const int wmin = ifd::fused_strip_width(64);  // the narrowest strips
     for (const CavDev &cv : h->cav)
-      cap += ((cv.nx + 55) / 56) * std::max(1, std::min((cv.ny + rmin - 1) / rmin, cv.ny / 2));
+      cap += ((cv.nx + wmin - 1) / wmin) *
+             std::max(1, std::min((cv.ny + rmin - 1) / rmin, cv.ny / 2));
     h->task_cap = std::max(cap, 1);
   }
   auto A = [&](size_t bytes) { return dalloc(h, bytes); };
@@ -991,7 +992,6 @@ int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best) {
   const int nts[3] = {64, 128, 256};
   const int rows[4] = {16, 32, 64, 128};
   for (int nt : nts) {
-    if (nt == 256 && h->precision == IFDLBM_FP64) continue;
     for (int r : rows)
       for (int sc = IFDLBM_SCHED_GRID; sc <= IFDLBM_SCHED_DYNAMIC; ++sc) {
         if ((rc = build_fused_tasks(h, nt, r, sc))) goto done;

@@ -1,26 +1,33 @@
 // Fused IFDLBM step: Steps (2)-(6) and the residual partials in one launch.
 //
-// A CTA of NT threads owns a strip [i0, i1) of at most W = NT - 8 columns of
-// one cavity (one thread per column, plus 4 halo columns on each side that it
-// recomputes) and a segment [j0, j1) of rows. It marches up the rows;
-// iteration k runs
+// A CTA of NT threads owns a strip [i0, i1) of at most W = NT/2 - 8 columns
+// of one cavity and a segment [j0, j1) of rows. Two threads share each of its
+// NT/2 columns (the strip plus 4 recomputed halo columns on each side): half
+// h = 0 takes the even rows of the march, half h = 1 the odd ones. Iteration
+// k (k = j0 - 4, j0 - 2, ...) runs, in half h,
 //
-//   stage A  row k     moments, f^eq, lagged power-law lambda (FP64 power),
-//                      f-hat^+ (Eq. 2.15), f-bar^+ (Eq. 2.16)
-//   stage 1  row k-2   half step f-bar(t+dt/2) (Eq. 3.7), its moments,
-//                      f(t+dt/2) (Eq. 2.17); wall values by extrapolation
-//   stage 2  row k-4   full step f-hat(t+dt) (Eq. 3.6); wall values by
-//                      extrapolation (Step 6); residual partials
+//   stage A  row k + h     moments, f^eq, lagged power-law lambda (FP64 power),
+//                          f-hat^+ (Eq. 2.15), f-bar^+ (Eq. 2.16)
+//   stage 1  row k - 2 + h half step f-bar(t+dt/2) (Eq. 3.7), its moments,
+//                          f(t+dt/2) (Eq. 2.17); wall values by extrapolation
+//   stage 2  row k - 4 + h full step f-hat(t+dt) (Eq. 3.6); wall values by
+//                          extrapolation (Step 6); residual partials
 //
 // so that each node's state is read from and written to HBM once per step.
-// The state of the rows ahead is prefetched with cp.async into a shared
-// staging ring; f-bar^+, f(t+dt/2) and f-hat^+ of the last five rows live in
-// shared rings (slot = row mod 5), from which both the xi neighbours (other
-// threads) and the eta neighbours (same thread) are read. Wall nodes follow
-// the rule of the staged kernels: a side-wall node takes its inner neighbour
-// on the same row, a bottom/lid node the node (clamp(i, 1, nx-2), 1 or ny-2);
-// row 0 of f(t+dt/2) is made with row 1, row ny-1 one iteration after row
-// ny-2 (so that it never takes the ring slot of a row still in use).
+// Shared memory per column pair: six-row rings of f-bar^+ and f(t+dt/2)
+// (slot = row mod 6), read across columns (xi stencils) and across the two
+// halves (eta stencils); and, per thread, five slots that hold the state of a
+// row from its cp.async prefetch (two iterations ahead) until stage A, and
+// then, in place, its f-hat^+ until the full step two iterations later. That
+// is ~410 B per thread in FP32, so that 16 warps fit on an SM. Four barriers
+// per iteration (two per row) order the stages across the halves.
+//
+// Wall nodes follow the rule of the staged kernels: a side-wall node takes
+// its inner neighbour on the same row, a bottom/lid node the node
+// (clamp(i, 1, nx-2), 1 or ny-2); row 0 of f(t+dt/2) is made with row 1 and
+// row ny-1 at the position of the march where it would be computed. The
+// full-step values of columns 1 and nx-2, which the wall columns extrapolate
+// from, are published through a small shared array.
 //
 // FP64 work per node is kept to the power of Eq. (1.4) and the residual
 // accumulation: GB300 issues FP64 at 1/64 of the FP32 rate.
@@ -34,21 +41,20 @@ namespace ifd {
 
 namespace {
 
-constexpr int STAGE_ROWS = 3;  // depth of the cp.async prefetch ring (2 rows ahead)
+constexpr int PF = 5;     // per-thread row slots: prefetched state, then f-hat^+
+constexpr int RING = 6;   // rows of the f-bar^+ and f(t+dt/2) rings
 
-// Shared state per column thread: ~700 B in FP32, so that five 64-thread
-// CTAs fit on an SM.
 template <class T, int NT>
 struct FusedSmem {
-  T st_g[STAGE_ROWS][9][NT];      // prefetched state g(t) of rows ahead
-  T fb[5][9][NT];                 // f-bar^+
-  T fh[5][9][NT];                 // f(t + dt/2)
-  T fp[5][9][NT];                 // f-hat^+ (its moments are u, P at t: Eqs. 2.10-2.11)
-  T lam[5][NT];                   // lambda(t)
-  T gn[9][NT];                    // f-hat(t + dt) of the current stage-2 row
+  static constexpr int NC = NT / 2;
+  T sf[PF][9][NT];        // per thread: g(t) of its rows, then f-hat^+ in place
+  T fb[RING][9][NC];      // f-bar^+
+  T fh[RING][9][NC];      // f(t + dt/2)
+  T edge[2][3][NC];       // u, v, P(t) of rows 0 and ny-1 (wall-row residuals)
+  T gw[2][2][9];          // f-hat(t+dt) of columns 1 and nx-2, per half
 };
 
-__device__ __forceinline__ int slot5(int r) { return (r + 10) % 5; }
+__device__ __forceinline__ int slot6(int r) { return (r + 12) % RING; }
 
 // c xi_x of row j and the Jacobian x_xi H: FP64 metrics for FP64 arithmetic,
 // their rounded float copies for FP32 arithmetic.
@@ -70,14 +76,14 @@ __device__ __forceinline__ T row_jac(const Geo &g, const CavDev &cv, int j) {
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
   if (bytes == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
   else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
 // Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side known
@@ -105,14 +111,14 @@ __device__ __forceinline__ T dmix2_sel(T fm2, T fm1, T f0, T fp1, T fp2, bool po
 }
 
 // c_{q xi} D_xi F + c_{q eta} D_eta F at an interior node: `row` is the xi
-// row of plane q (this thread at index t), `col` the five eta neighbours.
+// row of plane q (this thread at column lane l), `col` the five eta neighbours.
 template <int Q, class T>
-__device__ __forceinline__ T advect_q(const T *row, int t, const T col[5], T A, T B, T ceta_unit,
+__device__ __forceinline__ T advect_q(const T *row, int l, const T col[5], T A, T B, T ceta_unit,
                                       bool clo, bool chi, bool lo, bool hi, T eta_b, T i2dxi,
                                       T i2deta) {
   const T cxi = T(ex(Q)) * A - T(ey(Q)) * B;
   const T f0 = col[2];
-  T adv = cxi * dmix2_sel(row[t - 2], row[t - 1], f0, row[t + 1], row[t + 2], cxi >= T(0), clo,
+  T adv = cxi * dmix2_sel(row[l - 2], row[l - 1], f0, row[l + 1], row[l + 2], cxi >= T(0), clo,
                           chi, eta_b) * i2dxi;
   if constexpr (ey(Q) != 0) {
     const T ceta = T(ey(Q)) * ceta_unit;
@@ -123,20 +129,21 @@ __device__ __forceinline__ T advect_q(const T *row, int t, const T col[5], T A, 
   return adv;
 }
 
-template <class T, int Q, int NT>
+// out[q] = base_q - scale * advection_q for q = Q..8; ring planes are RS
+// apart, base planes BS apart.
+template <class T, int Q, int RS, int BS>
 struct AdvectAll {
-  // fills out[q] = F_q - scale * advection_q for q = Q..8
-  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int t, T A, T B,
+  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int l, T A, T B,
                                              T ceta_unit, bool clo, bool chi, bool lo, bool hi,
                                              T eta_b, T i2dxi, T i2deta, T scale, const T *base,
                                              T out[9]) {
-    const T col[5] = {cols[0][Q * NT], cols[1][Q * NT], cols[2][Q * NT], cols[3][Q * NT],
-                      cols[4][Q * NT]};
-    out[Q] = base[Q * NT] - scale * advect_q<Q>(rows + Q * NT, t, col, A, B, ceta_unit, clo, chi,
+    const T col[5] = {cols[0][Q * RS], cols[1][Q * RS], cols[2][Q * RS], cols[3][Q * RS],
+                      cols[4][Q * RS]};
+    out[Q] = base[Q * BS] - scale * advect_q<Q>(rows + Q * RS, l, col, A, B, ceta_unit, clo, chi,
                                                 lo, hi, eta_b, i2dxi, i2deta);
     if constexpr (Q < 8)
-      AdvectAll<T, Q + 1, NT>::run(rows, cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b, i2dxi,
-                                   i2deta, scale, base, out);
+      AdvectAll<T, Q + 1, RS, BS>::run(rows, cols, l, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
+                                       i2dxi, i2deta, scale, base, out);
   }
 };
 
@@ -180,18 +187,21 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 
 template <class T, int NT>
 __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
+  constexpr int NC = NT / 2;
   const Task task = a.tasks[ti];
   const CavDev &cv = a.cav[task.cav];
   const int i0 = task.i0, i1 = task.i1, j0 = task.j0, j1 = task.j1;
   const int nx = cv.nx, ny = cv.ny;
   const int t = threadIdx.x;
-  const int c = i0 - 4 + t;                          // this thread's column
+  const int h = t / NC;                              // row parity of this thread (warp-uniform)
+  const int l = t - h * NC;                          // column lane
+  const int c = i0 - 4 + l;                          // this thread's column
   const int cc = min(max(c, 0), nx - 1);             // clamped column for loads
   const bool colv = c >= 0 && c < nx;
-  const bool own = colv && c >= i0 && c < i1;        // output column (i1 - i0 <= NT - 8)
+  const bool own = colv && c >= i0 && c < i1;        // output column (i1 - i0 <= NC - 8)
   const bool inner_c = c >= 1 && c <= nx - 2;
   const bool wall_c = c == 0 || c == nx - 1;
-  const int tn = t + (min(max(c, 1), nx - 2) - c);   // thread of the inner neighbour column
+  const int ln = l + (min(max(c, 1), nx - 2) - c);   // lane of the inner neighbour column
   const bool clo = c == 1, chi = c == nx - 2;
 
   const int64_t b9 = 9 * cv.off;
@@ -210,41 +220,45 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 
   Partial p = {0, 0, 0, 0, 0, 0, 0};
   Leaf<T> leaf;
-  T u0s = T(0), v0s = T(0), P0s = T(0);              // u, v, P(t) of row 0
 
-  const int kb = j0 - 4, ke = j1 + 3;
-  const int rlo = max(kb, 0), rhi = min(ke, ny - 1);  // rows stage A needs
-  auto prefetch = [&](int r) {
+  const int kb = j0 - 4;
+  const int rlo = max(kb, 0), rhi = min(j1 + 3, ny - 1);   // rows of stage A
+  const int mlo = max(1, j0 - 2), mhi = min(ny - 2, j1 + 1);  // rows of the half step
+  const int olo = max(1, j0), ohi = min(ny - 2, j1 - 1);      // rows of the full step
+  const int nit = (j1 + 3 - kb) / 2 + 1;                      // k = kb + 2 it, it < nit
+  auto row_of = [&](int it) { return kb + 2 * it + h; };      // this thread's stage-A row
+  auto prefetch = [&](int it) {
+    const int r = row_of(it);
     if (r >= rlo && r <= rhi) {
-      const int s = r % STAGE_ROWS;
+      const int s = it % PF;
       const int64_t node = int64_t(r) * cv.pitch + cc;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) cp_async(&S.st_g[s][q][t], gin + q * cv.plane + node, sizeof(T));
+      for (int q = 0; q < 9; ++q) cp_async(&S.sf[s][q][t], gin + q * cv.plane + node, sizeof(T));
     }
     cp_commit();
   };
-  // lambda_prev of the row Step (2) works on next, loaded one row ahead
+  // lambda_prev of a row Step (2) works on, loaded one iteration ahead
   auto lam_load = [&](int r) {
     return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * cv.pitch + cc] : 0.0;
   };
-  // per-cavity constants of the relaxation time, converted once
+  // per-cavity constants of the relaxation time
   const double gmin2 = cv.gmin2, half_nm1 = cv.half_nm1, Kics2 = cv.Kics2;
   const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
-  // Step (2) for row r from the staging ring: moments, f^eq and lambda(t).
-  // lambda of row k + 1 is formed during the full step of row k, so that the
-  // FP64 power overlaps FP32 work instead of delaying the row it belongs to.
+  // Step (2) for this thread's row of iteration `it`: moments, f^eq and
+  // lambda(t). The row of iteration it + 1 is formed during the full step of
+  // iteration it, so that the FP64 power overlaps FP32 work.
   T nux = 0, nuy = 0, nP = 0, ngeq[9];
   double nlam = 0.0;
   struct Collided {
     T ux, uy, P, geq[9];
     double lam;
   };
-  auto collide = [&](int r, double lam_prev) {
+  auto collide = [&](int it, double lam_prev) {
     Collided o;
-    const int s = (r + STAGE_ROWS) % STAGE_ROWS;
+    const int s = it % PF;
     T g[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) g[q] = S.st_g[s][q][t];
+    for (int q = 0; q < 9; ++q) g[q] = S.sf[s][q][t];
     moments(g, c_, cs2, o.ux, o.uy, o.P);                 // Eqs. (2.10)-(2.11)
     equilibrium(o.P, o.ux, o.uy, c_, ics2, o.geq);        // Eq. (2.8)
     T d[9];
@@ -268,121 +282,134 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     for (int q = 0; q < 9; ++q) ngeq[q] = o.geq[q];
     nlam = o.lam;
   };
-#pragma unroll
-  for (int r = 0; r < STAGE_ROWS - 1; ++r) prefetch(kb + r);
-  cp_wait<STAGE_ROWS - 2>();
-  if (kb >= 0 && kb < ny) take(collide(kb, lam_load(kb)));
-  double lp_next = lam_load(kb + 1);  // lambda_prev of row k + 1
+  auto in_a = [&](int r) { return r >= rlo && r <= rhi; };
 
-  for (int k = kb; k <= ke; ++k) {
-    prefetch(k + STAGE_ROWS - 1);
-    cp_wait<STAGE_ROWS - 2>();                     // rows k and k + 1 have landed (own column)
+  prefetch(0);
+  prefetch(1);
+  cp_wait<1>();
+  if (in_a(row_of(0))) take(collide(0, lam_load(row_of(0))));
+  double lp_next = lam_load(row_of(1));  // lambda_prev of the next row
+  T Lprev = T(0);                        // lambda(t) of this thread's previous row
 
-    // ---------------- stage A: row k (lambda formed in the previous iteration) ----------------
-    if (k >= 0 && k < ny) {
-      const int s = k % STAGE_ROWS, sA = slot5(k);
-      if (own && k >= j0 && k < j1) lam_out[int64_t(k) * cv.pitch + c] = nlam;
+  for (int it = 0; it < nit; ++it) {
+    const int k = kb + 2 * it;
+
+    // ---------------- stage A: row k + h (lambda formed in the previous iteration) ----------------
+    const int ar = k + h;
+    T Lcur = T(0);
+    if (in_a(ar)) {
+      const int s = it % PF, sb = slot6(ar);
+      if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * cv.pitch + c] = nlam;
       const T L = T(nlam);
+      Lcur = L;
       const T i2 = T(1) / (T(2) * L + dt);
       const T ap = (T(2) * L - dt) * i2, bp = T(2) * dt * i2;  // Eq. (2.15)
       const T i4 = T(0.5) * i2;
       const T ab = (T(4) * L - dt) * i4, bb = T(3) * dt * i4;  // Eq. (2.16)
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const T gq = S.st_g[s][q][t];
-        S.fb[sA][q][t] = ab * gq + bb * ngeq[q];
-        S.fp[sA][q][t] = ap * gq + bp * ngeq[q];
+        const T gq = S.sf[s][q][t];
+        S.fb[sb][q][l] = ab * gq + bb * ngeq[q];
+        S.sf[s][q][t] = ap * gq + bp * ngeq[q];             // f-hat^+ in place of g
       }
-      S.lam[sA][t] = L;
-      if (k == 0) {
-        u0s = nux;
-        v0s = nuy;
-        P0s = nP;
+      if (ar == 0 || ar == ny - 1) {
+        const int e = ar == 0 ? 0 : 1;
+        S.edge[e][0][l] = nux;
+        S.edge[e][1][l] = nuy;
+        S.edge[e][2][l] = nP;
       }
     }
-    // No barrier: stage A writes only this thread's column of row k; other
-    // threads read a ring row across columns only two iterations later.
+    __syncthreads();  // f-bar^+ of rows k, k + 1
+    // the slot this prefetch fills was last read before the barrier above
+    prefetch(it + 2);
 
-    // ---------------- stage 1: row m = k - 2 ----------------
-    const int m = k - 2;
-    const bool do1 = m >= 1 && m <= ny - 2;
-    if (do1 && inner_c && t >= 2 && t < NT - 2) {
-      const int sm = slot5(m), sm1 = slot5(m - 1), sm2 = slot5(m - 2), sp1 = slot5(m + 1),
-                sp2 = slot5(m + 2);
+    // ---------------- stage 1: row m = k - 2 + h ----------------
+    const int m = k - 2 + h;
+    const bool do1 = m >= mlo && m <= mhi;
+    if (do1 && inner_c && l >= 2 && l < NC - 2) {
+      const int sm = slot6(m);
       const T A = row_cxix<T>(a.geo, cv, m);           // c xi_x
       const T B = A * xeH;                             // c xi_x x_eta / H
       const bool lo = m == 1, hi = m == ny - 2;
       T fbar[9];
-      fbar[0] = S.fb[sm][0][t];
+      fbar[0] = S.fb[sm][0][l];
       {
-        const T *cols[5] = {&S.fb[sm2][0][t], &S.fb[sm1][0][t], &S.fb[sm][0][t], &S.fb[sp1][0][t],
-                            &S.fb[sp2][0][t]};
-        AdvectAll<T, 1, NT>::run(&S.fb[sm][0][0], cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
-                                 i2dxi, i2deta, hdt, &S.fb[sm][0][t], fbar);   // Eq. (3.7)
+        const T *cols[5] = {&S.fb[slot6(m - 2)][0][l], &S.fb[slot6(m - 1)][0][l], &S.fb[sm][0][l],
+                            &S.fb[slot6(m + 1)][0][l], &S.fb[slot6(m + 2)][0][l]};
+        AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
+                                     eta_b, i2dxi, i2deta, hdt, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
       }
       T ux, uy, P;
       moments(fbar, c_, cs2, ux, uy, P);
       T geq[9];
       equilibrium(P, ux, uy, c_, ics2, geq);
-      const T L = S.lam[sm][t];
+      const T L = Lprev;                                 // lambda(t) of row m
       const T i4 = T(1) / (T(4) * L + dt);
-      const T ah = T(4) * L * i4, bh = dt * i4;                       // Eq. (2.17)
+      const T ah = T(4) * L * i4, bh = dt * i4;          // Eq. (2.17)
 #pragma unroll
-      for (int q = 0; q < 9; ++q) S.fh[sm][q][t] = ah * fbar[q] + bh * geq[q];
+      for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = ah * fbar[q] + bh * geq[q];
     }
-    __syncthreads();
-    if (m >= 1 && m < ny && t >= 2 && t < NT - 2 && colv) {
+    Lprev = Lcur;
+    __syncthreads();  // f(t + dt/2) of rows m
+
+    // ---------------- walls of f(t + dt/2) ----------------
+    if (l >= 2 && l < NC - 2 && colv) {
       if (do1 && wall_c) {                            // side walls of row m
         T F[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) F[q] = S.fh[slot5(m)][q][tn];
+        for (int q = 0; q < 9; ++q) F[q] = S.fh[slot6(m)][q][ln];
         nee(F, T(0), T(0), cv);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) S.fh[slot5(m)][q][t] = F[q];
+        for (int q = 0; q < 9; ++q) S.fh[slot6(m)][q][l] = F[q];
       }
-      if (m == 1 || m == ny - 1) {                    // bottom row 0 / lid row ny-1
-        const bool lid = m == ny - 1;
-        const int src = lid ? slot5(ny - 2) : slot5(1), dst = lid ? slot5(ny - 1) : slot5(0);
+      const bool bottom = m == 1 && do1;
+      const bool lid = m == ny - 1 && mhi == ny - 2 && mlo <= ny - 2;
+      if (bottom || lid) {                            // row 0 from row 1, row ny-1 from ny-2
+        const int src = lid ? slot6(ny - 2) : slot6(1), dst = lid ? slot6(ny - 1) : slot6(0);
         T F[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) F[q] = S.fh[src][q][tn];
+        for (int q = 0; q < 9; ++q) F[q] = S.fh[src][q][ln];
         nee(F, (lid && inner_c) ? T(cv.U) : T(0), T(0), cv);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) S.fh[dst][q][t] = F[q];
+        for (int q = 0; q < 9; ++q) S.fh[dst][q][l] = F[q];
       }
     }
-    // No barrier: stage 2 reads other columns only of row k - 4, finished two
-    // iterations ago, and the eta neighbours from its own column.
+    __syncthreads();  // wall values of f(t + dt/2)
 
-    // ---------------- stage 2: row o = k - 4 ----------------
-    const int o = k - 4;
-    const bool do2 = o >= 1 && o <= ny - 2 && o >= j0 && o < j1;
-    if (do2 && inner_c && t >= 4 && t < NT - 4) {
-      const int so = slot5(o), so1 = slot5(o - 1), so2 = slot5(o - 2), sp1 = slot5(o + 1),
-                sp2 = slot5(o + 2);
+    // ---------------- stage 2: row o = k - 4 + h ----------------
+    const int o = k - 4 + h;
+    const bool do2 = o >= olo && o <= ohi;
+    const int sp = (it + PF - 2) % PF;               // f-hat^+ of row o (iteration it - 2)
+    cp_wait<1>();                                    // this thread's row of iteration it + 1
+    T gnv[9];
+    if (do2 && inner_c && l >= 4 && l < NC - 4) {
+      const int so = slot6(o);
       const T A = row_cxix<T>(a.geo, cv, o);
       const T B = A * xeH;
       const bool lo = o == 1, hi = o == ny - 2;
-      T gnv[9];
-      gnv[0] = S.fp[so][0][t];
+      gnv[0] = S.sf[sp][0][t];
       {
-        const T *cols[5] = {&S.fh[so2][0][t], &S.fh[so1][0][t], &S.fh[so][0][t], &S.fh[sp1][0][t],
-                            &S.fh[sp2][0][t]};
-        AdvectAll<T, 1, NT>::run(&S.fh[so][0][0], cols, t, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
-                                 i2dxi, i2deta, dt, &S.fp[so][0][t], gnv);     // Eq. (3.6)
+        const T *cols[5] = {&S.fh[slot6(o - 2)][0][l], &S.fh[slot6(o - 1)][0][l], &S.fh[so][0][l],
+                            &S.fh[slot6(o + 1)][0][l], &S.fh[slot6(o + 2)][0][l]};
+        AdvectAll<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
+                                     eta_b, i2dxi, i2deta, dt, &S.sf[sp][0][t], gnv);  // Eq. (3.6)
       }
+      if (clo || chi) {                                // values the wall columns extrapolate
 #pragma unroll
-      for (int q = 0; q < 9; ++q) S.gn[q][t] = gnv[q];
+        for (int q = 0; q < 9; ++q) S.gw[h][chi ? 1 : 0][q] = gnv[q];
+      }
     }
-    if (k + 1 <= rhi && k + 1 >= 0) take(collide(k + 1, lp_next));  // lambda of the next row
-    lp_next = lam_load(k + 2);
-    __syncthreads();
+    if (in_a(row_of(it + 1))) take(collide(it + 1, lp_next));  // lambda of the next row
+    lp_next = lam_load(row_of(it + 2));
+    __syncthreads();  // f-hat(t + dt) of columns 1 and nx-2
+
     if (do2 && own) {
-      const int so = slot5(o);
-      T gnv[9];
+      if (wall_c) {
+        const int side = c == 0 ? 0 : 1;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) gnv[q] = S.gn[q][tn];
-      if (wall_c) nee(gnv, T(0), T(0), cv);
+        for (int q = 0; q < 9; ++q) gnv[q] = S.gw[h][side][q];
+        nee(gnv, T(0), T(0), cv);
+      }
       const int64_t node = int64_t(o) * cv.pitch + c;
 #pragma unroll
       for (int q = 0; q < 9; ++q) gout[q * cv.plane + node] = gnv[q];
@@ -391,7 +418,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         moments(gnv, c_, cs2, ux, uy, P);
         T fpo[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fpo[q] = S.fp[so][q][t];
+        for (int q = 0; q < 9; ++q) fpo[q] = S.sf[sp][q][t];
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
         const T wJ = wx * wy_in * row_jac<T>(a.geo, cv, o);
         leaf_add(leaf, p, ux, uy, P, u0, v0, P0, wJ, a.status);
@@ -401,8 +428,14 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const bool top = o == ny - 2 && j1 == ny;
       if (bottom || top) {
         T F[9];
+        if (wall_c) {
+          const int side = c == 0 ? 0 : 1;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) F[q] = S.gn[q][tn];
+          for (int q = 0; q < 9; ++q) F[q] = S.gw[h][side][q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < 9; ++q) F[q] = gnv[q];
+        }
         nee(F, (top && inner_c) ? T(cv.U) : T(0), T(0), cv);
         const int r = bottom ? 0 : ny - 1;
         const int64_t nd = int64_t(r) * cv.pitch + c;
@@ -411,15 +444,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         if (a.want_residual) {
           T wx2, wy2, wP2;
           moments(F, c_, cs2, wx2, wy2, wP2);
-          T ou = u0s, ov = v0s, oP = P0s;
-          if (!bottom) {
-            T fpr[9];
-#pragma unroll
-            for (int q = 0; q < 9; ++q) fpr[q] = S.fp[slot5(r)][q][t];
-            moments(fpr, c_, cs2, ou, ov, oP);
-          }
+          const int e = bottom ? 0 : 1;
           const T wJ = wx * wy_edge * row_jac<T>(a.geo, cv, r);
-          leaf_add(leaf, p, wx2, wy2, wP2, ou, ov, oP, wJ, a.status);
+          leaf_add(leaf, p, wx2, wy2, wP2, S.edge[e][0][l], S.edge[e][1][l], S.edge[e][2][l], wJ,
+                   a.status);
         }
       }
     }
@@ -434,12 +462,19 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   __syncthreads();  // the next task reuses the shared rings
 }
 
+// Launch bounds: 16 resident warps per SM in FP32 (registers capped at 128),
+// 8 in FP64 (its shared rings are twice as large).
+template <class T, int NT>
+struct Occ {
+  static constexpr int blocks = (sizeof(T) == 4 ? 512 : 256) / NT > 0 ? (sizeof(T) == 4 ? 512 : 256) / NT : 1;
+};
+
 // Schedules: 0 one CTA per task; 1 persistent CTAs taking positions
 // blockIdx.x, blockIdx.x + gridDim.x, ... of the largest-first order;
 // 2 persistent CTAs taking positions from an atomic counter (no waiting on
 // other CTAs: a CTA that finds the list exhausted returns).
 template <class T, int NT>
-__global__ void __launch_bounds__(NT) k_fused(FusedArgs a) {
+__global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
   __shared__ int next;
@@ -491,9 +526,7 @@ template <class T> int fused_blocks_per_sm(int nt) {
   switch (nt) {
     case 64: return blocks_per_sm_nt<T, 64>();
     case 128: return blocks_per_sm_nt<T, 128>();
-    case 256:
-      if constexpr (sizeof(T) == 4) return blocks_per_sm_nt<T, 256>();
-      return 0;
+    case 256: return blocks_per_sm_nt<T, 256>();
   }
   return 0;
 }
@@ -502,7 +535,7 @@ template <class T> int fused_smem_bytes(int nt) {
   switch (nt) {
     case 64: return int(sizeof(FusedSmem<T, 64>));
     case 128: return int(sizeof(FusedSmem<T, 128>));
-    case 256: return sizeof(T) == 4 ? int(sizeof(FusedSmem<T, 256>)) : -1;
+    case 256: return int(sizeof(FusedSmem<T, 256>));
   }
   return -1;
 }
@@ -511,12 +544,7 @@ template <class T> bool launch_fused(const FusedArgs &a, int nt, int ntasks, cud
   switch (nt) {
     case 64: launch_fused_nt<T, 64>(a, ntasks, s); return true;
     case 128: launch_fused_nt<T, 128>(a, ntasks, s); return true;
-    case 256:
-      if constexpr (sizeof(T) == 4) {
-        launch_fused_nt<T, 256>(a, ntasks, s);
-        return true;
-      }
-      return false;
+    case 256: launch_fused_nt<T, 256>(a, ntasks, s); return true;
   }
   return false;
 }

@@ -101,7 +101,9 @@ struct FusedArgs {
   int want_residual;
 };
 
-// Fused kernel (fused.cu); nt in {64, 128, 256} (256 in FP32 only).
+// Fused kernel (fused.cu); nt in {64, 128, 256} threads, two per column: a
+// CTA's strip holds nt/2 - 8 output columns plus a 4-column halo on each side.
+constexpr int fused_strip_width(int nt) { return nt / 2 - 8; }
 template <class T> bool launch_fused(const FusedArgs &a, int nt, int ntasks, cudaStream_t s);
 template <class T> int fused_smem_bytes(int nt);
 template <class T> int fused_blocks_per_sm(int nt);

@@ -1,0 +1,76 @@
+"""Steady fields: the sm_103a library against the oracle's steady state.
+
+65 x 65 cavity, theta = 60 deg, n = 0.75, Re = 100 (the FP64 validation
+case), advanced from rest for the number of steps stored with the oracle's
+fields (tests/golden/make_steady_fields.py calls only the oracle; the per-step
+max-norm residual there is ~1e-11). Bars:
+
+* FP64 (staged and fused): u, v, psi within 1e-12 of max|field|; P within
+  1e-12 of the magnitude of its Eq. (2.11) terms, c_s^2/|wbar_0| sum_{i>0} w_i
+  rho0 (P is a small difference of O(w_i) sums).
+* FP32 deviation storage (FP64 power law and reductions): u, v, P, psi within
+  1e-5 of max|field|.
+
+A steady state is an attractor of the step, so rounding differences do not
+grow along the run; the FP64 bar is the per-step bar.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = "steady_65_theta60_n075_re100.npz"
+KERNELS = {"staged": dict(kernel="staged"), "fused": dict(kernel="fused")}
+
+
+def _golden(golden_dir):
+    d = np.load(os.path.join(golden_dir, GOLDEN))
+    nx, ny, Re, n, th = d["case"]
+    return d, (int(nx), int(ny), float(Re), float(n), float(th))
+
+
+def _run(case, steps, **kw):
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    nx, ny, Re, n, th = case
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=th)], **kw)
+    done = 0
+    while done < steps:
+        k = min(10000, steps - done)
+        s.step(k)
+        done += k
+    r = s.residual()[0]
+    m = s.macros(0)
+    s.close()
+    m["P"] = (m["rho"] - 1.0) / 3.0   # the ABI reports rho = rho0 + P / c_s^2 (c = 1, rho0 = 1)
+    return m, r
+
+
+def _p_scale():
+    """c_s^2/|wbar_0| times the sum of the rest populations i > 0 (c = 1, rho0 = 1)."""
+    rest = O.equilibrium(np.zeros(1), np.zeros(1), np.zeros(1))[:, 0]
+    return (1.0 / 3.0) / abs(O.OMEGA_BAR[0]) * rest[1:].sum()
+
+
+@pytest.mark.parametrize("kname", list(KERNELS))
+def test_steady_fp64_fields_match_oracle(golden_dir, kname):
+    d, case = _golden(golden_dir)
+    m, r = _run(case, int(d["steps"]), precision="fp64", **KERNELS[kname])
+    for k in ("u", "v", "psi"):
+        err = np.abs(m[k] - d[k]).max() / np.abs(d[k]).max()
+        assert err <= 1e-12, (k, err)
+    assert np.abs(m["P"] - d["P"]).max() <= 1e-12 * _p_scale()
+    # the last step's residuals (Eq. 2.19) are those of a converged run
+    Eu, EP, Rinf = d["last_residual"]
+    assert r[2] <= 10 * Rinf + 1e-13, (r[2], Rinf)
+
+
+@pytest.mark.parametrize("kname", list(KERNELS))
+def test_steady_fp32_deviation_error(golden_dir, kname):
+    d, case = _golden(golden_dir)
+    m, _ = _run(case, int(d["steps"]), precision="fp32dev", **KERNELS[kname])
+    errs = {k: np.abs(m[k] - d[k]).max() / np.abs(d[k]).max() for k in ("u", "v", "P", "psi")}
+    assert all(e <= 1e-5 for e in errs.values()), errs
