@@ -420,7 +420,8 @@ def run_adjoint_measure(nx=257, ny=257, T=2000, every=100, n=0.75, Re=400.0, the
     from paper_2306_07603_gb300.adjoint import KineticEnergy
     from paper_2306_07603_gb300.solver import Solver, cavity
 
-    s = Solver([cavity(nx, ny, Re, n, theta_deg=theta)], precision="fp64", kernel="staged")
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=theta)], precision="fp64", kernel="staged",
+               dt_mode="grid")   # the time-step rule the adjoint uses (dt independent of theta)
     s.step(2)
     s.sync()
     t0 = time.perf_counter()

@@ -49,9 +49,13 @@ extern "C" {
 /* Storage / arithmetic form of the distributions (pattern "precision"). */
 #define IFDLBM_FP64 0    /* f-hat and all arithmetic in FP64 */
 #define IFDLBM_FP32DEV 1 /* f-hat stored and updated in FP32 as deviations
-                            g_i = f-hat_i - w_i rho0 from the rest equilibrium
-                            (Eq. 2.8 at P = 0, u = 0); metrics, the power-law
-                            relaxation time and all reductions in FP64 */
+                            g_i = f-hat_i - f^eq_i(P_ref, 0) from the rest
+                            equilibrium at a reference pressure (Eq. 2.8 at
+                            u = 0), P_ref re-based on the cavity's mean
+                            pressure every 1024 steps (a uniform pressure
+                            offset is a neutral, drifting mode); metrics, the
+                            power-law relaxation time and all reductions in
+                            FP64. Every output includes P_ref. */
 
 /* Step kernel organisation. */
 #define IFDLBM_KERNEL_AUTO 0   /* FUSED for FP32DEV, STAGED for FP64 */
@@ -90,10 +94,13 @@ typedef struct {
 } ifdlbm_options;
 
 /* Time-step rules ("c = 1, CFL = 0.5", Sec. 5.1). */
-#define IFDLBM_DT_GRID 0          /* dt = cfl * min(L/(nx-1), H/(ny-1)) / c (default) */
+#define IFDLBM_DT_GRID 0          /* dt = cfl * min(L/(nx-1), H/(ny-1)) / c; on a skewed
+                                     grid the contravariant Courant numbers exceed cfl
+                                     and the two-stage scheme relies on collisions to
+                                     stay stable (it fails for lambda/dt >~ 1) */
 #define IFDLBM_DT_CONTRAVARIANT 1 /* dt = cfl * min(dxi / max|c_xi|, deta / max|c_eta|),
                                      the Courant number of the contravariant speeds
-                                     of Eq. (3.4); needed for theta < 45 deg */
+                                     of Eq. (3.4) (default); equal to GRID at 90 deg */
 
 /* Cavity-to-CTA schedules of the fused kernel. Tasks are strips of columns x
  * segments of rows of every cavity of the batch. */
@@ -295,7 +302,7 @@ int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double
 
 /* Autotuner of the batched fused step (pattern "batching"): times
  * `trial_steps` >= 1 steps of every combination of fused_threads {64, 128,
- * 256 (FP32DEV only)}, rows per task {16, 32, 64, 128} and schedule {GRID,
+ * 256}, rows per task {16, 32, 64, 128} and schedule {GRID,
  * STATIC, DYNAMIC} on the handle's own cavities, starting each trial from
  * the same saved state, and keeps the fastest. The state is restored
  * afterwards, so the call does not advance the simulation. Needs a handle
@@ -323,6 +330,18 @@ int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best);
 int ifdlbm_adjoint_seed_energy(ifdlbm_handle h, const void *state, void *adj, double *dparams);
 int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double *dparams);
 
+/* Seed for J = sum over cavities k of psi_k(i_k, j_k), the stream function
+ * (psi = 0 on the bottom wall, trapezoidal rule along xi = const lines) at
+ * one node per cavity given in the HOST array nodes[2k] = i_k, nodes[2k+1] =
+ * j_k (0 <= i_k < nx, 0 <= j_k < ny). With the node of the primary eddy
+ * (ifdlbm_eddies(...)[0].i, .j) this is the gradient of psi_min, the
+ * primary-vortex strength, wherever its minimising node does not change.
+ * Writes adj = dJ/dstate and adds the direct theta term (through x_eta of
+ * Eq. 3.8.2) to dparams. Asynchronous; INVALID_ARG for a node outside its
+ * cavity. */
+int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes, void *adj,
+                            double *dparams);
+
 /* Self-test of the FP64 power used for Eq. (1.4): for n DEVICE doubles x
  * (finite, > 0) writes fast[k] = the library's table-driven x^m and
  * ref[k] = CUDA's pow(x[k], m), on the handle's stream (no sync). */
@@ -332,6 +351,42 @@ int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, doubl
 /* Number of kernel launches the library has enqueued since the process
  * started (graph replays count every kernel node). */
 int64_t ifdlbm_launch_count(void);
+
+/* Eddy centres of a steady cavity flow, as tabulated in Tables 1-3 (Sec. 5.1):
+ * the primary eddy and the two counter-rotating bottom-corner eddies.
+ *
+ *  - primary: the interior node (0 < i < nx-1, 0 < j < ny-1) of smallest psi
+ *    (psi = 0 on the bottom wall and d psi = u dy - v dx, so the clockwise
+ *    eddy of a lid moving in +x has psi < 0);
+ *  - bottom-left / bottom-right: among interior nodes with eta <= 1/2 and
+ *    xi < 1/2 (left) or xi >= 1/2 (right), the strict local maximum of psi
+ *    (larger than its 8 neighbours) with the largest psi > 0.
+ *
+ * Each centre is refined below the grid spacing by the least-squares
+ * quadratic psi ~ a + b s + c t + d s^2 + e s t + f t^2 over the 3 x 3 nodes
+ * around the extremum node (s, t its offsets in nodes), taking the
+ * stationary point when the quadratic has one there of the same kind within
+ * one node, else the node itself. xi = (i + s)/(nx-1), eta = (j + t)/(ny-1)
+ * are mapped to (x, y) by the map of Eq. (3.8.1) with the cavity's L, H and
+ * theta. */
+typedef struct {
+  double x, y;     /* physical centre */
+  double xi, eta;  /* computational coordinates of the centre */
+  double psi;      /* fitted psi at the centre */
+  int i, j;        /* extremum node */
+  int found;       /* 1 if the eddy exists, else 0 and the rest is zero */
+  int refined;     /* 1 if the quadratic fit moved the centre off the node */
+} ifdlbm_eddy;
+
+/* Host-only, no GPU: eddies of a HOST psi array [ny][nx] (nx, ny >= 3) of a
+ * cavity with geometry g. out[0] primary, out[1] bottom-left, out[2]
+ * bottom-right. */
+int ifdlbm_find_eddies(int nx, int ny, ifdlbm_geometry g, const double *psi,
+                       ifdlbm_eddy out[3]);
+
+/* The same for cavity `cavity` of a handle at its current state (forms psi
+ * as ifdlbm_batch_macros does; synchronises). */
+int ifdlbm_eddies(ifdlbm_handle h, int cavity, ifdlbm_eddy out[3]);
 
 #ifdef __cplusplus
 }

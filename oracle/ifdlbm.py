@@ -391,22 +391,29 @@ def periodic_grid(nx, ny, Lx=1.0, Ly=1.0, periodic_eta=True, c=1.0):
 
 
 def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None,
-                  gamma_min=None, dt=None, dt_mode="grid", grid=None):
+                  gamma_min=None, dt=None, dt_mode="contravariant", grid=None):
     """Parameters of a cavity run.
 
     * K from Re, Eq. (2.15.1).
-    * READING (time step): dt = CFL * min(L dxi, H deta) / c, with the
-      paper's c = 1 and CFL = 0.5 (Sec. 5.1) (dt_mode "grid"). With
-      dt_mode "contravariant" (and the cavity's Grid), the Courant number
-      applies to the contravariant speeds of Eq. (3.4):
+    * READING (time step, c = 1 and CFL = 0.5 of Sec. 5.1): the Courant
+      number applies to the contravariant speeds of Eq. (3.4), the speeds
+      the finite differences of the computational grid see:
       dt = CFL * min(dxi / max|c_xi|, deta / max|c_eta|), taken over all
-      nodes and directions.
+      nodes and directions (dt_mode "contravariant", needs the cavity's
+      Grid). On the skewed grid these speeds exceed c, and the rule
+      dt = CFL * min(L dxi, H deta) / c (dt_mode "grid") lets the two-stage
+      scheme amplify the diagonal populations (von Neumann factor up to
+      1.75 per step at theta = 60 deg); the 256^2, Re = 100, n >= 1
+      cavities of Tables 1-3 then diverge. At theta = 90 deg both rules
+      agree.
     * READING (blend): eta_b, which the paper leaves free in [0, 1], defaults
       to DEFAULT_ETA_B.
     * READING (zero-shear clamp): gamma_min defaults to 1e-3 U / H.
     """
     K = consistency_coefficient(Re, n, U, H)
     if dt is None and dt_mode == "contravariant":
+        if grid is None:
+            raise ValueError("dt_mode 'contravariant' needs the cavity's Grid")
         mxi = float(np.max(np.abs(_re(grid.cxi))))
         meta = float(np.max(np.abs(_re(grid.ceta))))
         dt = cfl * min(grid.dxi / mxi, grid.deta / meta)
@@ -641,6 +648,66 @@ def stream_function(ux, uy, g: Grid):
     psi = np.zeros_like(integrand)
     psi[1:] = np.cumsum(0.5 * (integrand[1:] + integrand[:-1]) * g.deta, axis=0)
     return psi
+
+
+def eddy_centres(psi, L=1.0, H=1.0, theta_deg=60.0):
+    """Centres of the primary and the two bottom-corner eddies (Tables 1-3).
+
+    READING (the paper tabulates the centres without saying how they were
+    located): the primary eddy is the interior node of smallest psi (the
+    clockwise eddy of a lid moving in +x); a corner eddy is, among interior
+    nodes with eta <= 1/2 and xi < 1/2 (left) or xi >= 1/2 (right), the strict
+    local maximum of psi (above its 8 neighbours) with the largest psi > 0.
+    Each node is refined by the least-squares quadratic
+    psi ~ a + b s + c t + d s^2 + e s t + f t^2 on its 3 x 3 neighbourhood
+    (s, t node offsets): its stationary point is taken when the Hessian has
+    the extremum's sign and the point lies within one node, else the node.
+    Returns [primary, left, right], each a dict (x, y, xi, eta, psi, i, j,
+    refined) or None.
+    """
+    psi = np.asarray(psi, dtype=float)
+    ny, nx = psi.shape
+    s_off, t_off = np.meshgrid([-1.0, 0.0, 1.0], [-1.0, 0.0, 1.0])
+    s_off, t_off = s_off.ravel(), t_off.ravel()
+    A = np.stack([np.ones(9), s_off, t_off, s_off ** 2, s_off * t_off, t_off ** 2], axis=1)
+
+    def refine(i, j, minimum):
+        patch = psi[j - 1:j + 2, i - 1:i + 2].ravel()
+        a, b, c, d, e, f = np.linalg.lstsq(A, patch, rcond=None)[0]
+        Hm = np.array([[2 * d, e], [e, 2 * f]])
+        s = t = 0.0
+        refined = False
+        det = np.linalg.det(Hm)
+        if det > 0 and ((2 * d > 0) if minimum else (2 * d < 0)):
+            st = np.linalg.solve(Hm, -np.array([b, c]))
+            if np.all(np.abs(st) <= 1.0):
+                s, t = st
+                refined = True
+        val = a + b * s + c * t + d * s * s + e * s * t + f * t * t if refined else psi[j, i]
+        xi_c, eta_c = (i + s) / (nx - 1), (j + t) / (ny - 1)
+        x, y = trapezoid_xy(xi_c, eta_c, L, H, theta_deg)
+        return dict(x=float(x), y=float(y), xi=xi_c, eta=eta_c, psi=float(val), i=i, j=j,
+                    refined=refined)
+
+    inner = psi[1:-1, 1:-1]
+    j0, i0 = np.unravel_index(np.argmin(inner), inner.shape)
+    out = [refine(i0 + 1, j0 + 1, True), None, None]
+    best = [None, None]
+    for j in range(1, ny - 1):
+        if 2 * j > ny - 1:
+            break
+        for i in range(1, nx - 1):
+            p = psi[j, i]
+            nb = psi[j - 1:j + 2, i - 1:i + 2].copy()
+            nb[1, 1] = -np.inf
+            if p > 0 and p > nb.max():
+                side = 0 if 2 * i < nx - 1 else 1
+                if best[side] is None or p > psi[best[side][1], best[side][0]]:
+                    best[side] = (i, j)
+    for side in (0, 1):
+        if best[side] is not None:
+            out[1 + side] = refine(best[side][0], best[side][1], False)
+    return out
 
 
 # ---------------------------------------------------------------------------

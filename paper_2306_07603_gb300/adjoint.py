@@ -1,14 +1,24 @@
-"""Gradients of the kinetic energy after T steps with respect to (n, Re, theta).
+"""Gradients of scalar objectives after T steps with respect to (n, Re, theta).
 
-``KineticEnergy.apply(params, spec, T, every)`` advances one cavity T steps
-from rest in FP64 (staged kernels) and returns the kinetic energy of
-Eq. (5.1); its backward pass runs the library's hand-written discrete
-adjoint (``ifdlbm_adjoint_step``) in reverse, recomputing the states of each
-segment of ``every`` steps from a checkpoint kept on the device. All
-arithmetic happens in libifdlbm.so; this module only orders the calls.
+Two objectives of one cavity advanced T steps from rest in FP64 (staged
+kernels):
+
+* ``KineticEnergy``: the kinetic energy of Eq. (5.1);
+* ``PsiMin``: psi_min, the stream function at the primary eddy's node (the
+  strength of the primary vortex), differentiable wherever that node does not
+  change under the perturbation.
+
+The forward pass keeps a device checkpoint of the state every ``every``
+steps; the backward pass seeds the adjoint of the final state with the
+library's seed for the objective, then runs the hand-written discrete adjoint
+(``ifdlbm_adjoint_step``) in reverse, recomputing the states of each segment
+from its checkpoint. All arithmetic happens in libifdlbm.so; this module only
+orders the calls. Sensitivities are taken at a fixed time step: the runs use
+the grid time-step rule, whose dt does not depend on theta.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import capi
@@ -20,55 +30,94 @@ def _state_buffer(h, stream):
         return torch.empty(capi.ifdlbm_state_bytes(h) // 8, dtype=torch.float64, device="cuda")
 
 
+def _forward(params, nx, ny, T, every, U_lid, L, H, eta_b):
+    n, Re, theta = (float(v) for v in params.detach().cpu().tolist())
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=theta, U_lid=U_lid, L=L, H=H)],
+               precision="fp64", kernel="staged", eta_b=eta_b, dt_mode="grid")
+    ckpt = {}
+    for t0 in range(0, T, every):
+        buf = _state_buffer(s.h, s.stream)
+        capi.ifdlbm_save_state_dev(s.h, buf)
+        ckpt[t0] = buf
+        s.step(min(every, T - t0))
+    final = _state_buffer(s.h, s.stream)
+    capi.ifdlbm_save_state_dev(s.h, final)
+    return s, ckpt, final
+
+
+def _backward(ctx, seed, gJ):
+    """Adjoint sweep: `seed(h, final, adj, dparams)` writes dJ/d(final state)."""
+    s, T, every = ctx.solver, ctx.T, ctx.every
+    with torch.cuda.stream(s.stream):
+        dparams = torch.zeros(3, dtype=torch.float64, device="cuda")
+    adj = _state_buffer(s.h, s.stream)
+    seed(s.h, ctx.final, adj, dparams)
+    for t0 in sorted(ctx.ckpt, reverse=True):
+        t1 = min(t0 + every, T)
+        states = [ctx.ckpt[t0]]
+        capi.ifdlbm_load_state_dev(s.h, ctx.ckpt[t0])
+        for _ in range(t0 + 1, t1):             # recompute the segment
+            capi.ifdlbm_step(s.h, 1)
+            buf = _state_buffer(s.h, s.stream)
+            capi.ifdlbm_save_state_dev(s.h, buf)
+            states.append(buf)
+        for t in range(t1 - 1, t0 - 1, -1):
+            capi.ifdlbm_adjoint_step(s.h, states[t - t0], adj, dparams)
+    s.sync()
+    grad = dparams.cpu() * gJ
+    s.close()
+    return (grad,) + (None,) * 8
+
+
 class KineticEnergy(torch.autograd.Function):
     """J(n, Re, theta) = kinetic energy after T steps; params = tensor([n, Re, theta_deg])."""
 
     @staticmethod
     def forward(ctx, params, nx, ny, T, every, U_lid=0.1, L=1.0, H=1.0, eta_b=0.5):
-        n, Re, theta = (float(v) for v in params.detach().cpu().tolist())
-        s = Solver([cavity(nx, ny, Re, n, theta_deg=theta, U_lid=U_lid, L=L, H=H)],
-                   precision="fp64", kernel="staged", eta_b=eta_b)
-        ckpt = {}
-        for t0 in range(0, T, every):
-            buf = _state_buffer(s.h, s.stream)
-            capi.ifdlbm_save_state_dev(s.h, buf)
-            ckpt[t0] = buf
-            s.step(min(every, T - t0))
-        final = _state_buffer(s.h, s.stream)
-        capi.ifdlbm_save_state_dev(s.h, final)
+        s, ckpt, final = _forward(params, nx, ny, T, every, U_lid, L, H, eta_b)
         J = float(s.residual()[0][3])
         ctx.solver, ctx.ckpt, ctx.final, ctx.T, ctx.every = s, ckpt, final, T, every
         return torch.tensor(J, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, gJ):
-        s, T, every = ctx.solver, ctx.T, ctx.every
-        with torch.cuda.stream(s.stream):
-            dparams = torch.zeros(3, dtype=torch.float64, device="cuda")
-        adj = _state_buffer(s.h, s.stream)
-        capi.ifdlbm_adjoint_seed_energy(s.h, ctx.final, adj, dparams)
-        for t0 in sorted(ctx.ckpt, reverse=True):
-            t1 = min(t0 + every, T)
-            states = [ctx.ckpt[t0]]
-            capi.ifdlbm_load_state_dev(s.h, ctx.ckpt[t0])
-            for _ in range(t0 + 1, t1):             # recompute the segment
-                capi.ifdlbm_step(s.h, 1)
-                buf = _state_buffer(s.h, s.stream)
-                capi.ifdlbm_save_state_dev(s.h, buf)
-                states.append(buf)
-            for t in range(t1 - 1, t0 - 1, -1):
-                capi.ifdlbm_adjoint_step(s.h, states[t - t0], adj, dparams)
-        s.sync()
-        grad = dparams.cpu() * gJ
-        s.close()
-        return (grad,) + (None,) * 8
+        return _backward(ctx, capi.ifdlbm_adjoint_seed_energy, gJ)
+
+
+class PsiMin(torch.autograd.Function):
+    """J(n, Re, theta) = min over interior nodes of psi after T steps."""
+
+    @staticmethod
+    def forward(ctx, params, nx, ny, T, every, U_lid=0.1, L=1.0, H=1.0, eta_b=0.5):
+        s, ckpt, final = _forward(params, nx, ny, T, every, U_lid, L, H, eta_b)
+        e = s.eddies(0)[0]
+        psi = np.zeros((ny, nx))
+        capi.ifdlbm_batch_macros(s.h, 0, None, None, None, psi)
+        ctx.node = (e.i, e.j)
+        ctx.solver, ctx.ckpt, ctx.final, ctx.T, ctx.every = s, ckpt, final, T, every
+        return torch.tensor(float(psi[e.j, e.i]), dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gJ):
+        node = ctx.node
+        return _backward(
+            ctx, lambda h, st, adj, dp: capi.ifdlbm_adjoint_seed_psi(h, st, [node], adj, dp), gJ)
+
+
+_OBJECTIVES = {"energy": KineticEnergy, "psi_min": PsiMin}
+
+
+def objective_and_gradient(objective, n, Re, theta_deg, nx, ny, T, every=100, **kw):
+    """(J, dJ/dn, dJ/dRe, dJ/dtheta_deg) through the adjoint; objective in
+    {"energy", "psi_min"}."""
+    p = torch.tensor([n, Re, theta_deg], dtype=torch.float64, requires_grad=True)
+    J = _OBJECTIVES[objective].apply(p, nx, ny, T, every,
+                                     *(kw.get(k, d) for k, d in (("U_lid", 0.1), ("L", 1.0),
+                                                                 ("H", 1.0), ("eta_b", 0.5))))
+    J.backward()
+    return float(J), *(float(v) for v in p.grad)
 
 
 def energy_and_gradient(n, Re, theta_deg, nx, ny, T, every=100, **kw):
-    """(J, dJ/dn, dJ/dRe, dJ/dtheta_deg) through the adjoint."""
-    p = torch.tensor([n, Re, theta_deg], dtype=torch.float64, requires_grad=True)
-    J = KineticEnergy.apply(p, nx, ny, T, every, *(kw.get(k, d) for k, d in
-                                                   (("U_lid", 0.1), ("L", 1.0), ("H", 1.0),
-                                                    ("eta_b", 0.5))))
-    J.backward()
-    return float(J), *(float(v) for v in p.grad)
+    """(J, dJ/dn, dJ/dRe, dJ/dtheta_deg) of the kinetic energy through the adjoint."""
+    return objective_and_gradient("energy", n, Re, theta_deg, nx, ny, T, every, **kw)

@@ -73,6 +73,12 @@ class ifdlbm_tuning(C.Structure):
                 ("pad", C.c_int)]
 
 
+class ifdlbm_eddy(C.Structure):
+    _fields_ = [("x", C.c_double), ("y", C.c_double), ("xi", C.c_double), ("eta", C.c_double),
+                ("psi", C.c_double), ("i", C.c_int), ("j", C.c_int), ("found", C.c_int),
+                ("refined", C.c_int)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -108,7 +114,10 @@ _SIGS = {
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
+    "ifdlbm_adjoint_seed_psi": (C.c_int, [_H, _P, C.c_void_p, _P, _P]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
+    "ifdlbm_find_eddies": (C.c_int, [C.c_int, C.c_int, ifdlbm_geometry, _P, C.c_void_p]),
+    "ifdlbm_eddies": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_profile_read": (C.c_int, [_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
 }
 
@@ -297,6 +306,13 @@ def ifdlbm_adjoint_seed_energy(h, state, adj, dparams):
                                                             _ptr(dparams)), h)
 
 
+def ifdlbm_adjoint_seed_psi(h, state, nodes, adj, dparams):
+    """nodes: sequence of (i, j) per cavity."""
+    arr = (C.c_int * (2 * len(nodes)))(*[int(v) for ij in nodes for v in ij])
+    return _check(load_library().ifdlbm_adjoint_seed_psi(h, _ptr(state), arr, _ptr(adj),
+                                                         _ptr(dparams)), h)
+
+
 def ifdlbm_adjoint_step(h, state_n, adj, dparams):
     return _check(load_library().ifdlbm_adjoint_step(h, _ptr(state_n), _ptr(adj), _ptr(dparams)), h)
 
@@ -316,3 +332,18 @@ def ifdlbm_profile_read(h, kernel):
     n = C.c_int64()
     _check(load_library().ifdlbm_profile_read(h, int(kernel), C.byref(ms), C.byref(n)), h)
     return ms.value, n.value
+
+
+def ifdlbm_find_eddies(nx, ny, geometry, psi):
+    """Host-only: (primary, bottom-left, bottom-right) eddies of a [ny][nx] psi array."""
+    out = (ifdlbm_eddy * 3)()
+    g = ifdlbm_geometry(*geometry) if not isinstance(geometry, ifdlbm_geometry) else geometry
+    _check(load_library().ifdlbm_find_eddies(int(nx), int(ny), g, _ptr(psi), out))
+    return list(out)
+
+
+def ifdlbm_eddies(h, cavity=0):
+    """(primary, bottom-left, bottom-right) eddies of cavity `cavity` of a handle."""
+    out = (ifdlbm_eddy * 3)()
+    _check(load_library().ifdlbm_eddies(h, int(cavity), out), h)
+    return list(out)

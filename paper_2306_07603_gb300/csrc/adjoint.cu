@@ -229,6 +229,39 @@ __global__ void k_adj_seed_energy(AdjArgs a) {
   tile_sum3(0.0, 0.0, dth, a.ppart, 3);
 }
 
+// Seed of J = sum over cavities of psi(i*, j*), the stream function at one
+// node per cavity (the primary eddy's node for J = psi_min). psi(i, j) =
+// sum_{m <= j} w_m deta (u H - v x_eta(xi_i)) with trapezoid weights w_m
+// (1/2 at m = 0 and m = j), so dJ/dg_q = w_m deta c (H e_qx - x_eta e_qy) on
+// column i*, rows m <= j*, and zero elsewhere; theta enters directly through
+// x_eta = H cot(theta) (2 xi - 1).
+__global__ void k_adj_seed_psi(AdjArgs a) {
+  const Ref r = tile_ref(a.tile_cav, a.cav);
+  const CavDev &cv = a.cav[r.cav];
+  double dth = 0.0;
+  if (r.valid) {
+    const int64_t node = int64_t(r.j) * cv.pitch + r.i;
+    const int is = a.psi_nodes[2 * r.cav], js = a.psi_nodes[2 * r.cav + 1];
+    double *ag = a.adj_g + 9 * cv.off;
+    double w = 0.0;
+    if (r.i == is && r.j <= js && js > 0) w = ((r.j == 0 || r.j == js) ? 0.5 : 1.0) * cv.deta;
+    const double xe = a.geo.xeta[cv.goff + r.i];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) ag[q * cv.plane + node] = w * cv.c * (cv.H * ex(q) - xe * ey(q));
+    a.adj_lam[cv.off + node] = 0.0;
+    if (w != 0.0) {
+      const double *g = a.g + 9 * cv.off;
+      double gg[9];
+#pragma unroll
+      for (int q = 0; q < 9; ++q) gg[q] = g[q * cv.plane + node];
+      double ux, uy, P;
+      moments(gg, cv.c, cv.cs2, ux, uy, P);
+      dth = -w * uy * cv.H * (2.0 * r.i * cv.dxi - 1.0) * cv.dcot;
+    }
+  }
+  tile_sum3(0.0, 0.0, dth, a.ppart, 3);
+}
+
 // A3 walls: adjoint of g_{n+1} at interior nodes next to walls += X^T(walls).
 __global__ void k_adj3_walls(AdjArgs a) {
   const Ref r = tile_ref(a.tile_cav, a.cav);
@@ -478,6 +511,13 @@ static const dim3 kT(TILE_X, TILE_Y);
 void launch_adjoint_seed(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s) {
   cudaMemsetAsync(a.ppart, 0, size_t(ntiles) * 12 * sizeof(double), s);
   k_adj_seed_energy<<<ntiles, kT, 0, s>>>(a);
+  k_adj_reduce<<<ncav, 128, 0, s>>>(a.cav, a.ppart, dparams);
+}
+
+void launch_adjoint_seed_psi(const AdjArgs &a, int ntiles, int ncav, double *dparams,
+                             cudaStream_t s) {
+  cudaMemsetAsync(a.ppart, 0, size_t(ntiles) * 12 * sizeof(double), s);
+  k_adj_seed_psi<<<ntiles, kT, 0, s>>>(a);
   k_adj_reduce<<<ncav, 128, 0, s>>>(a.cav, a.ppart, dparams);
 }
 

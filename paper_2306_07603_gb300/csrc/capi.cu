@@ -53,12 +53,14 @@ struct ifdlbm_ctx {
   // adjoint scratch (allocated on the first adjoint call)
   double *adj_g1 = nullptr, *adj_l1 = nullptr, *adj_fhb = nullptr, *adj_fbarb = nullptr,
          *adj_fbb = nullptr, *adj_lamb2 = nullptr, *adj_ppart = nullptr;
+  int *adj_nodes = nullptr;  // [ncav][2] nodes of the psi objective
   int64_t total_plane = 0;
   int64_t geo_len = 0;
   int64_t max_n2 = 0;
   double *stage = nullptr;  // staging for host transfers: 10 * max_n2 doubles
   int cur = 0;
   int64_t steps = 0;
+  int64_t rebased_at = 0;  // step count of the last re-basing (FP32DEV)
   int64_t bytes = 0;
   int64_t h2d_bytes = 0;
   std::vector<Alloc> allocs;
@@ -187,6 +189,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.part = h->b.part;
     f.status = h->b.status;
     f.powtab = h->b.powtab;
+    f.pref = h->b.pref;
     f.want_residual = want_residual ? 1 : 0;
     if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
     timed(h, IFDLBM_KPROF_FUSED, [&] { ifd::launch_fused<T>(f, h->fused_nt, h->grid, h->stream); });
@@ -211,6 +214,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
   a.part = h->b.part;
   a.status = h->b.status;
   a.powtab = h->b.powtab;
+  a.pref = h->b.pref;
   a.want_residual = want_residual ? 1 : 0;
   timed(h, IFDLBM_KPROF_COLLIDE, [&] { ifd::launch_collide<T>(a, h->ntiles, h->stream); });
   timed(h, IFDLBM_KPROF_HALF, [&] { ifd::launch_half<T>(a, h->ntiles, h->stream); });
@@ -370,7 +374,7 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   opt->fused_threads = 0;
   opt->fused_rows = 0;
   opt->schedule = IFDLBM_SCHED_GRID;
-  opt->dt_mode = IFDLBM_DT_GRID;
+  opt->dt_mode = IFDLBM_DT_CONTRAVARIANT;
   return IFDLBM_OK;
 }
 
@@ -570,6 +574,8 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   ok &= geof != nullptr;
   ok &= (h->stage = (double *)A(size_t(10 * h->max_n2) * sizeof(double))) != nullptr;
   ok &= (h->b.powtab = (double *)A(ifd::POW_TABLE_SIZE * sizeof(double))) != nullptr;
+  ok &= (h->b.pref = (double *)A(size_t(ncav) * sizeof(double))) != nullptr;
+  ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
   if (!ok) {
     release_all(h);
     delete h;
@@ -638,6 +644,9 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.status, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.pref, 0, size_t(ncav) * sizeof(double), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(h->b.ptile, 0, size_t(h->ntiles + ncav) * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.g[0], 0, 9 * off * tsize, s);
   if (e == cudaSuccess) {
     if (h->precision == IFDLBM_FP64)
@@ -670,6 +679,20 @@ int ifdlbm_create(int nx, int ny, ifdlbm_geometry g, double Re, double n, double
   return ifdlbm_create_batch(1, &c, opt, stream, out);
 }
 
+// FP32 storage: every REBASE_EVERY steps the stored deviations are re-based
+// on the cavity's mean pressure (launch_rebase), so that the drift of that
+// neutral mode does not enlarge |g| and with it the FP32 rounding. The
+// state (f-hat) is unchanged, apart from one rounding of g.
+constexpr int64_t REBASE_EVERY = 1024;
+
+static void maybe_rebase(ifdlbm_ctx *h) {
+  if (h->precision != IFDLBM_FP32DEV || h->steps - h->rebased_at < REBASE_EVERY) return;
+  ifd::launch_rebase<float>(h->b.cav, h->b.tile_cav, h->b.g[h->cur], h->b.pref, h->b.ptile,
+                            h->ntiles, h->ncav, h->stream);
+  g_launches += 3;
+  h->rebased_at = h->steps;
+}
+
 int ifdlbm_step(ifdlbm_handle h, int nsteps) {
   if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");
   if (nsteps < 0) return fail(h, IFDLBM_ERR_INVALID_ARG, "nsteps must be >= 0");
@@ -686,6 +709,7 @@ int ifdlbm_step(ifdlbm_handle h, int nsteps) {
       g_launches += int64_t(chunk) * launches_per_step(h, false);
       remaining -= chunk;
       h->steps += chunk;
+      maybe_rebase(h);
     }
   }
   for (; remaining > 0; --remaining) {
@@ -693,6 +717,7 @@ int ifdlbm_step(ifdlbm_handle h, int nsteps) {
     g_launches += launches_per_step(h, false);
     h->cur ^= 1;
     h->steps += 1;
+    maybe_rebase(h);
   }
   enqueue_step_any(h, h->cur, true);
   g_launches += launches_per_step(h, true);
@@ -709,10 +734,10 @@ int ifdlbm_macros_dev(ifdlbm_handle h, int cavity, double *rho, double *u, doubl
   cudaSetDevice(h->device);
   const ifdlbm_cavity &s = h->spec[cavity];
   if (h->precision == IFDLBM_FP64)
-    ifd::launch_macros<double>(h->b.cav, h->b.geo, cavity, h->b.g[h->cur], rho, u, v, psi, s.nx,
+    ifd::launch_macros<double>(h->b.cav, h->b.geo, cavity, h->b.pref, h->b.g[h->cur], rho, u, v, psi, s.nx,
                                s.ny, h->stream);
   else
-    ifd::launch_macros<float>(h->b.cav, h->b.geo, cavity, h->b.g[h->cur], rho, u, v, psi, s.nx,
+    ifd::launch_macros<float>(h->b.cav, h->b.geo, cavity, h->b.pref, h->b.g[h->cur], rho, u, v, psi, s.nx,
                               s.ny, h->stream);
   g_launches += 1;
   cudaError_t e = cudaGetLastError();
@@ -742,6 +767,17 @@ int ifdlbm_macros(ifdlbm_handle h, double *rho, double *u, double *v, double *ps
   return ifdlbm_batch_macros(h, 0, rho, u, v, psi);
 }
 
+int ifdlbm_eddies(ifdlbm_handle h, int cavity, ifdlbm_eddy out[3]) {
+  if (!cavity_ok(h, cavity) || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle, cavity or out");
+  const ifdlbm_cavity &s = h->spec[cavity];
+  std::vector<double> psi(size_t(s.nx) * s.ny);
+  int rc = ifdlbm_batch_macros(h, cavity, nullptr, nullptr, nullptr, psi.data());
+  if (rc) return rc;
+  rc = ifdlbm_find_eddies(s.nx, s.ny, s.geom, psi.data(), out);
+  if (rc) return fail(h, rc, "eddies: " + std::string(ifdlbm_last_error(nullptr)));
+  return IFDLBM_OK;
+}
+
 int ifdlbm_batch_residual(ifdlbm_handle h, double *out) {
   if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
   cudaSetDevice(h->device);
@@ -766,10 +802,10 @@ int ifdlbm_get_state(ifdlbm_handle h, int cavity, double *fhat, double *lambda_p
   const ifdlbm_cavity &s = h->spec[cavity];
   const int64_t n2 = int64_t(s.nx) * s.ny;
   if (h->precision == IFDLBM_FP64)
-    ifd::launch_export<double>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+    ifd::launch_export<double>(h->b.cav, cavity, h->b.pref, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
                                h->stage + 9 * n2, s.nx, s.ny, h->stream);
   else
-    ifd::launch_export<float>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+    ifd::launch_export<float>(h->b.cav, cavity, h->b.pref, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
                               h->stage + 9 * n2, s.nx, s.ny, h->stream);
   g_launches += 1;
   cudaError_t e = cudaGetLastError();
@@ -795,10 +831,10 @@ int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const doub
                         cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state copy");
   if (h->precision == IFDLBM_FP64)
-    ifd::launch_import<double>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+    ifd::launch_import<double>(h->b.cav, cavity, h->b.pref, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
                                h->stage + 9 * n2, s.nx, s.ny, h->stream);
   else
-    ifd::launch_import<float>(h->b.cav, cavity, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
+    ifd::launch_import<float>(h->b.cav, cavity, h->b.pref, h->b.g[h->cur], h->b.lam[h->cur], h->stage,
                               h->stage + 9 * n2, s.nx, s.ny, h->stream);
   g_launches += 1;
   e = cudaGetLastError();
@@ -810,7 +846,8 @@ int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const doub
 int64_t ifdlbm_state_bytes(ifdlbm_handle h) {
   if (!h) return -1;
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
-  return int64_t(9 * h->total_plane * tsize + h->total_plane * sizeof(double));
+  return int64_t(9 * h->total_plane * tsize + h->total_plane * sizeof(double) +
+                 h->ncav * sizeof(double));
 }
 
 int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst) {
@@ -818,9 +855,13 @@ int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst) {
   cudaSetDevice(h->device);
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
   const size_t gb = 9 * h->total_plane * tsize;
+  const size_t lb = h->total_plane * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(dst, h->b.g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync((char *)dst + gb, h->b.lam[h->cur], h->total_plane * sizeof(double),
+    e = cudaMemcpyAsync((char *)dst + gb, h->b.lam[h->cur], lb, cudaMemcpyDeviceToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char *)dst + gb + lb, h->b.pref, h->ncav * sizeof(double),
                         cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "save_state_dev");
   return IFDLBM_OK;
@@ -831,9 +872,13 @@ int ifdlbm_load_state_dev(ifdlbm_handle h, const void *src) {
   cudaSetDevice(h->device);
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
   const size_t gb = 9 * h->total_plane * tsize;
+  const size_t lb = h->total_plane * sizeof(double);
   cudaError_t e = cudaMemcpyAsync(h->b.g[h->cur], src, gb, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->b.lam[h->cur], (const char *)src + gb, h->total_plane * sizeof(double),
+    e = cudaMemcpyAsync(h->b.lam[h->cur], (const char *)src + gb, lb, cudaMemcpyDeviceToDevice,
+                        h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.pref, (const char *)src + gb + lb, h->ncav * sizeof(double),
                         cudaMemcpyDeviceToDevice, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "load_state_dev");
   return IFDLBM_OK;
@@ -896,6 +941,7 @@ int adjoint_ready(ifdlbm_ctx *h) {
   ok &= (h->adj_fbb = (double *)dalloc(h, 9 * P)) != nullptr;
   ok &= (h->adj_lamb2 = (double *)dalloc(h, P)) != nullptr;
   ok &= (h->adj_ppart = (double *)dalloc(h, size_t(h->ntiles) * 12 * sizeof(double))) != nullptr;
+  ok &= (h->adj_nodes = (int *)dalloc(h, size_t(h->ncav) * 2 * sizeof(int))) != nullptr;
   if (!ok) return fail(h, IFDLBM_ERR_OOM, "adjoint: device allocation failed");
   for (double *p : {h->adj_fhb, h->adj_fbarb, h->adj_fbb})
     cudaMemsetAsync(p, 0, 9 * P, h->stream);
@@ -940,6 +986,31 @@ int ifdlbm_adjoint_seed_energy(ifdlbm_handle h, const void *state, void *adj, do
   return IFDLBM_OK;
 }
 
+int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes, void *adj,
+                            double *dparams) {
+  if (!h || !state || !nodes || !adj || !dparams)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  for (int k = 0; k < h->ncav; ++k) {
+    const ifdlbm_cavity &c = h->spec[k];
+    if (nodes[2 * k] < 0 || nodes[2 * k] >= c.nx || nodes[2 * k + 1] < 0 || nodes[2 * k + 1] >= c.ny)
+      return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint_seed_psi: node outside its cavity");
+  }
+  cudaSetDevice(h->device);
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  // pageable source: the copy is staged before the call returns
+  cudaError_t e = cudaMemcpyAsync(h->adj_nodes, nodes, size_t(h->ncav) * 2 * sizeof(int),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint_seed_psi nodes");
+  ifd::AdjArgs a = adj_args(h, state, adj);
+  a.psi_nodes = h->adj_nodes;
+  ifd::launch_adjoint_seed_psi(a, h->ntiles, h->ncav, dparams, h->stream);
+  g_launches += 2;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint seed psi");
+  return IFDLBM_OK;
+}
+
 int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double *dparams) {
   if (!h || !state_n || !adj || !dparams) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
   cudaSetDevice(h->device);
@@ -961,6 +1032,7 @@ int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double 
   f.part = h->b.part;
   f.status = h->b.status;
   f.powtab = h->b.powtab;
+  f.pref = h->b.pref;
   f.want_residual = 0;
   ifd::launch_collide<double>(f, h->ntiles, h->stream);
   ifd::launch_half<double>(f, h->ntiles, h->stream);

@@ -29,16 +29,38 @@ __host__ __device__ constexpr double wbar(int i) {
   return i == 0 ? -5.0 / 9.0 : (i <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
 }
 
+// FP32 arithmetic keeps the moment identities of Eqs. (2.8), (2.10)-(2.11)
+// free of systematic error: the weights are carried as the integers 36 w_i
+// and 36 wbar_i, and the non-representable factors 1/36 and 1/5 as pairs of
+// floats (hi + lo, ~48 bits), so that the only FP32 errors left are the
+// roundings of the operations. A fixed relative error in a weight (1/9 and
+// 1/36 are not floats) would make the collision drive u and P towards
+// (1 + delta) u and (1 + delta) P every step, a bias that the slowest modes
+// of a cavity integrate over thousands of steps.
+struct F2 {
+  float hi, lo;
+};
+__host__ __device__ constexpr F2 f2_of(double x) { return {float(x), float(x - double(float(x)))}; }
+constexpr F2 INV36 = f2_of(1.0 / 36.0);
+constexpr F2 INV5 = f2_of(1.0 / 5.0);
+__device__ __forceinline__ float mul_f2(float x, F2 k) { return fmaf(x, k.hi, x * k.lo); }
+__host__ __device__ constexpr int w36(int i) { return i == 0 ? 16 : (i <= 4 ? 4 : 1); }
+__host__ __device__ constexpr int wbar36(int i) { return i == 0 ? -20 : (i <= 4 ? 4 : 1); }
+
 // Velocity and pressure of a deviation set, Eqs. (2.10)-(2.11):
 //   u = c sum_i e_i g_i,
-//   P = c_s^2 / wbar_0 (-sum_{i>0} g_i + w_0 |u|^2 / (2 c_s^2)).
+//   P = c_s^2 / wbar_0 (-sum_{i>0} g_i + w_0 |u|^2 / (2 c_s^2))
+//     = (3 c^2 sum_{i>0} g_i - 2 |u|^2) / 5            (c_s^2 = c^2/3).
 template <class T>
 __device__ __forceinline__ void moments(const T g[9], T c, T cs2, T &ux, T &uy, T &P) {
   ux = c * ((g[1] - g[3]) + (g[5] - g[6]) + (g[8] - g[7]));
   uy = c * ((g[2] - g[4]) + (g[5] + g[6]) - (g[7] + g[8]));
   T s = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
   T uu = ux * ux + uy * uy;
-  P = (cs2 / T(wbar(0))) * (-s + T(wgt(0)) * uu / (T(2) * cs2));
+  if constexpr (sizeof(T) == 4)
+    P = mul_f2(T(3) * (c * c) * s - T(2) * uu, INV5);
+  else
+    P = (cs2 / T(wbar(0))) * (-s + T(wgt(0)) * uu / (T(2) * cs2));
 }
 
 // Designed equilibrium, Eq. (2.8) (quadratic term over 2 c_s^4), minus w_i rho0.
@@ -52,8 +74,21 @@ __device__ __forceinline__ void equilibrium(T P, T ux, T uy, T c, T inv_cs2, T g
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const T cu = c * (T(ex(i)) * ux + T(ey(i)) * uy);
-    geq[i] = T(wbar(i)) * pterm + T(wgt(i)) * (cu * inv_cs2 + cu * cu * half_inv_cs4 + base);
+    const T quad = cu * inv_cs2 + cu * cu * half_inv_cs4 + base;
+    if constexpr (sizeof(T) == 4)
+      geq[i] = mul_f2(T(wbar36(i)) * pterm + T(w36(i)) * quad, INV36);
+    else
+      geq[i] = T(wbar(i)) * pterm + T(wgt(i)) * quad;
   }
+}
+
+// The transforms of Eqs. (2.15)-(2.17) have coefficients summing to one,
+// a F + b f^eq with a = 1 - b; they are evaluated as F + b (f^eq - F), so
+// that u and P, which F and f^eq share, are kept to the rounding of the
+// small difference rather than of F.
+template <class T>
+__device__ __forceinline__ T toward(T F, T feq, T b) {
+  return F + b * (feq - F);
 }
 
 // Relaxation time of Step (2): strain rate from f^ne (Eqs. 2.12-2.13, with

@@ -167,16 +167,19 @@ __device__ __forceinline__ void leaf_flush(Leaf<T> &l, Partial &p) {
   l.n = 0;
 }
 
+// P1, P0 are pressures of the stored deviations; Pr their reference (the
+// pressure of Eq. 2.11 is Pr + P), which cancels in the difference.
 template <class T>
 __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P1, T u0, T v0,
-                                         T P0, T wJ, unsigned *status) {
+                                         T P0, T Pr, T wJ, unsigned *status) {
   if (!(isfinite(u1) && isfinite(v1))) atomicOr(status, 1u);
   const T du = u1 - u0, dv = v1 - v0, dP = P1 - P0;
   const T du2 = du * du + dv * dv, u2 = u1 * u1 + v1 * v1;
+  const T Pf = P1 + Pr;
   l.du2 += du2;
   l.u2 += u2;
   l.dP2 += dP * dP;
-  l.P2 += P1 * P1;
+  l.P2 += Pf * Pf;
   l.ek += T(0.5) * wJ * u2;
   l.du2max = max(l.du2max, du2);
   l.u2max = max(l.u2max, u2);
@@ -217,6 +220,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T ceta_unit = T(cv.c / cv.H);
   const T xeH = T(a.geo.xeH[cv.goff + cc]);          // x_eta / H of this column
   const T wx = T(((c == 0 || c == nx - 1) ? 0.5 : 1.0) * cv.dxi);
+  const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
   Partial p = {0, 0, 0, 0, 0, 0, 0};
   Leaf<T> leaf;
@@ -303,14 +307,13 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const T L = T(nlam);
       Lcur = L;
       const T i2 = T(1) / (T(2) * L + dt);
-      const T ap = (T(2) * L - dt) * i2, bp = T(2) * dt * i2;  // Eq. (2.15)
-      const T i4 = T(0.5) * i2;
-      const T ab = (T(4) * L - dt) * i4, bb = T(3) * dt * i4;  // Eq. (2.16)
+      const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
+      const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt) = bb
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         const T gq = S.sf[s][q][t];
-        S.fb[sb][q][l] = ab * gq + bb * ngeq[q];
-        S.sf[s][q][t] = ap * gq + bp * ngeq[q];             // f-hat^+ in place of g
+        S.fb[sb][q][l] = toward(gq, ngeq[q], bb);
+        S.sf[s][q][t] = toward(gq, ngeq[q], bp);          // f-hat^+ in place of g
       }
       if (ar == 0 || ar == ny - 1) {
         const int e = ar == 0 ? 0 : 1;
@@ -344,10 +347,9 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       T geq[9];
       equilibrium(P, ux, uy, c_, ics2, geq);
       const T L = Lprev;                                 // lambda(t) of row m
-      const T i4 = T(1) / (T(4) * L + dt);
-      const T ah = T(4) * L * i4, bh = dt * i4;          // Eq. (2.17)
+      const T bh = dt / (T(4) * L + dt);                 // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
 #pragma unroll
-      for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = ah * fbar[q] + bh * geq[q];
+      for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = toward(fbar[q], geq[q], bh);
     }
     Lprev = Lcur;
     __syncthreads();  // f(t + dt/2) of rows m
@@ -421,7 +423,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         for (int q = 0; q < 9; ++q) fpo[q] = S.sf[sp][q][t];
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
         const T wJ = wx * wy_in * row_jac<T>(a.geo, cv, o);
-        leaf_add(leaf, p, ux, uy, P, u0, v0, P0, wJ, a.status);
+        leaf_add(leaf, p, ux, uy, P, u0, v0, P0, Pr, wJ, a.status);
       }
       // wall rows produced with their neighbour rows
       const bool bottom = o == 1 && j0 == 0;
@@ -446,8 +448,8 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
           moments(F, c_, cs2, wx2, wy2, wP2);
           const int e = bottom ? 0 : 1;
           const T wJ = wx * wy_edge * row_jac<T>(a.geo, cv, r);
-          leaf_add(leaf, p, wx2, wy2, wP2, S.edge[e][0][l], S.edge[e][1][l], S.edge[e][2][l], wJ,
-                   a.status);
+          leaf_add(leaf, p, wx2, wy2, wP2, S.edge[e][0][l], S.edge[e][1][l], S.edge[e][2][l], Pr,
+                   wJ, a.status);
         }
       }
     }

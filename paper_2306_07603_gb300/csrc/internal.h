@@ -59,6 +59,8 @@ struct Bufs {
   CavDev *cav;       // [ncav]
   Geo geo;
   double *powtab;    // tables of pow_fast (fastpow.cuh)
+  double *pref;      // [ncav] reference pressure: f-hat = w rho0 + wbar pref / c_s^2 + g
+  double *ptile;     // [ntiles + ncav] scratch of the re-basing reduction
 };
 
 struct StepArgs {
@@ -74,6 +76,7 @@ struct StepArgs {
   double *part;
   unsigned *status;
   const double *powtab;
+  const double *pref;  // [ncav] reference pressure of the stored deviations
   int want_residual;
 };
 
@@ -98,6 +101,7 @@ struct FusedArgs {
   double *part;
   unsigned *status;
   const double *powtab;
+  const double *pref;  // [ncav] reference pressure of the stored deviations
   int want_residual;
 };
 
@@ -128,8 +132,11 @@ struct AdjArgs {
   double *adj_g, *adj_lam;   // in: adjoint of state n + 1; out: of state n
   double *fhb, *fbarb, *fbb, *lamb2;  // adjoint scratch
   double *ppart;             // [ntiles][4 slots][3] parameter partials
+  const int *psi_nodes;      // [ncav][2] (i, j) of the psi objective (seed_psi only)
 };
 void launch_adjoint_seed(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s);
+void launch_adjoint_seed_psi(const AdjArgs &a, int ntiles, int ncav, double *dparams,
+                             cudaStream_t s);
 void launch_adjoint_step(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s);
 
 // Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
@@ -140,14 +147,24 @@ void launch_pow_selftest(int n, const double *x, double m, const double *tab, do
 // Utility kernels (staged.cu)
 template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,
                                     int ntiles, cudaStream_t s);
-template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const void *g,
+template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const double *pref,
+                                      const void *g,
                                       double *rho, double *u, double *v, double *psi,
                                       int nx, int ny, cudaStream_t s);
-template <class T> void launch_export(const CavDev *cav, int cavity, const void *g,
+template <class T> void launch_export(const CavDev *cav, int cavity, const double *pref,
+                                      const void *g,
                                       const double *lam, double *fhat, double *lamo, int nx,
                                       int ny, cudaStream_t s);
-template <class T> void launch_import(const CavDev *cav, int cavity, void *g, double *lam,
+template <class T> void launch_import(const CavDev *cav, int cavity, const double *pref,
+                                      void *g, double *lam,
                                       const double *fhat, const double *lami, int nx, int ny,
+                                      cudaStream_t s);
+// Re-bases the stored deviations of every cavity on its mean pressure:
+// shift = mean over the cavity's nodes of P(g), g_i -= wbar_i shift / c_s^2,
+// pref += shift (the state f-hat = w rho0 + wbar pref / c_s^2 + g is
+// unchanged). ptile: scratch of ntiles + ncav doubles.
+template <class T> void launch_rebase(const CavDev *cav, const int *tile_cav, void *g,
+                                      double *pref, double *ptile, int ntiles, int ncav,
                                       cudaStream_t s);
 
 // Records `msg` as the handle-less last error (ifdlbm_last_error(NULL)) and

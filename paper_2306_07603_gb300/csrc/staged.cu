@@ -85,15 +85,14 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_collide(StepArgs a) {
 
   const T L = T(lam), dt = T(cv.dt);
   const T i2 = T(1) / (T(2) * L + dt);
-  const T ap = (T(2) * L - dt) * i2, bp = T(2) * dt * i2;     // Eq. (2.15)
-  const T i4 = T(0.5) * i2;                                   // 1 / (4 lam + 2 dt)
-  const T ab = (T(4) * L - dt) * i4, bb = T(3) * dt * i4;     // Eq. (2.16)
+  const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
+  const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt), (4 lam - dt)/(4 lam + 2 dt) = 1 - bb
   T *fp = (T *)a.fp + b9;
   T *fb = (T *)a.fb + b9;
 #pragma unroll
   for (int q = 0; q < 9; ++q) {
-    fp[q * cv.plane + node] = ap * g[q] + bp * geq[q];
-    fb[q * cv.plane + node] = ab * g[q] + bb * geq[q];
+    fp[q * cv.plane + node] = toward(g[q], geq[q], bp);
+    fb[q * cv.plane + node] = toward(g[q], geq[q], bb);
   }
   double *m0 = a.m0 + 3 * cv.off;
   m0[node] = double(ux);
@@ -163,11 +162,10 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   T geq[9];
   equilibrium(P, ux, uy, c, ics2, geq);
   const T L = T(lam), dt = T(cv.dt);
-  const T i4 = T(1) / (T(4) * L + dt);
-  const T ah = T(4) * L * i4, bh = dt * i4;      // Eq. (2.17)
+  const T bh = dt / (T(4) * L + dt);             // Eq. (2.17): 4 lam/(4 lam + dt) = 1 - bh
   T fh[9];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) fh[q] = ah * fbar[q] + bh * geq[q];
+  for (int q = 0; q < 9; ++q) fh[q] = toward(fbar[q], geq[q], bh);
   if (wall) nee(fh, T(uwx), T(0), cv);
   store9((T *)a.fh + b9, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
 }
@@ -217,7 +215,8 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
       p.du2 = du * du + dv * dv;
       p.u2 = u1 * u1 + v1 * v1;
       p.dP2 = dP * dP;
-      p.P2 = P1 * P1;
+      const double Pfull = P1 + a.pref[r.cav];   // P of the deviations plus their reference
+      p.P2 = Pfull * Pfull;
       p.du2max = p.du2;
       p.u2max = p.u2;
       const double wx = ((r.i == 0 || r.i == cv.nx - 1) ? 0.5 : 1.0) * cv.dxi;
@@ -254,9 +253,10 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_init(const CavDev *cavs, con
 // One thread per xi = const line: macros at every node, then
 // psi_j = psi_{j-1} + (I_j + I_{j-1}) deta / 2 with I = u y_eta - v x_eta.
 template <class T>
-__global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const T *g, double *rho,
-                         double *u, double *v, double *psi) {
+__global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *pref, const T *g,
+                         double *rho, double *u, double *v, double *psi) {
   const CavDev &cv = cavs[cavity];
+  const double p0 = pref[cavity];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.nx) return;
   const T *gb = g + 9 * cv.off;
@@ -268,7 +268,7 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const T *g, do
     T ux, uy, P;
     moments(gg, T(cv.c), T(cv.cs2), ux, uy, P);
     const int64_t o = int64_t(j) * cv.nx + i;
-    if (rho) rho[o] = cv.rho0 + double(P) * cv.inv_cs2;
+    if (rho) rho[o] = cv.rho0 + (p0 + double(P)) * cv.inv_cs2;
     if (u) u[o] = double(ux);
     if (v) v[o] = double(uy);
     const double I = double(ux) * cv.H - double(uy) * xeta;
@@ -279,9 +279,10 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const T *g, do
 }
 
 template <class T>
-__global__ void k_export(const CavDev *cavs, int cavity, const T *g, const double *lam,
-                         double *fhat, double *lamo) {
+__global__ void k_export(const CavDev *cavs, int cavity, const double *pref, const T *g,
+                         const double *lam, double *fhat, double *lamo) {
   const CavDev &cv = cavs[cavity];
+  const double pt = pref[cavity] * cv.inv_cs2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= cv.nx) return;
   const int64_t node = int64_t(j) * cv.pitch + i, o = int64_t(j) * cv.nx + i;
@@ -289,22 +290,89 @@ __global__ void k_export(const CavDev *cavs, int cavity, const T *g, const doubl
   if (fhat)
 #pragma unroll
     for (int q = 0; q < 9; ++q)
-      fhat[q * n2 + o] = double(g[9 * cv.off + q * cv.plane + node]) + wgt(q) * cv.rho0;
+      fhat[q * n2 + o] = double(g[9 * cv.off + q * cv.plane + node]) + wgt(q) * cv.rho0 +
+                         wbar(q) * pt;
   if (lamo) lamo[o] = lam[cv.off + node];
 }
 
 template <class T>
-__global__ void k_import(const CavDev *cavs, int cavity, T *g, double *lam, const double *fhat,
-                         const double *lami) {
+__global__ void k_import(const CavDev *cavs, int cavity, const double *pref, T *g, double *lam,
+                         const double *fhat, const double *lami) {
   const CavDev &cv = cavs[cavity];
+  const double pt = pref[cavity] * cv.inv_cs2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
   if (i >= cv.nx) return;
   const int64_t node = int64_t(j) * cv.pitch + i, o = int64_t(j) * cv.nx + i;
   const int64_t n2 = int64_t(cv.nx) * cv.ny;
 #pragma unroll
   for (int q = 0; q < 9; ++q)
-    g[9 * cv.off + q * cv.plane + node] = T(fhat[q * n2 + o] - wgt(q) * cv.rho0);
+    g[9 * cv.off + q * cv.plane + node] = T(fhat[q * n2 + o] - wgt(q) * cv.rho0 - wbar(q) * pt);
   lam[cv.off + node] = lami[o];
+}
+
+// Re-basing of the stored deviations on the mean pressure (FP32 storage):
+// a uniform pressure offset is a neutral mode of the scheme that drifts, and
+// carrying it in every g_i would make the FP32 rounding of g grow with it.
+// k_psum: per tile, sum of P(g) in FP64; k_pshift: per cavity, the mean
+// (fixed-order sum over its tiles) into ptile[ntiles + k], pref += mean;
+// k_rebase: g_i -= wbar_i mean / c_s^2 at every node (one rounding).
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_psum(const CavDev *cavs, const int *tile_cav,
+                                                          const T *g, double *ptile) {
+  const NodeRef r = tile_node(tile_cav, cavs);
+  const CavDev &cv = cavs[r.cav];
+  double v = 0.0;
+  if (r.valid) {
+    T gg[9];
+    load9(g + 9 * cv.off, cv.plane, int64_t(r.j) * cv.pitch + r.i, gg);
+    T ux, uy, P;
+    moments(gg, T(cv.c), T(cv.cs2), ux, uy, P);
+    v = double(P);
+  }
+  __shared__ double sh[TILE_X * TILE_Y];
+  const int t = threadIdx.y * TILE_X + threadIdx.x;
+  sh[t] = v;
+  __syncthreads();
+  for (int w = TILE_X * TILE_Y / 2; w > 0; w >>= 1) {
+    if (t < w) sh[t] += sh[t + w];
+    __syncthreads();
+  }
+  if (t == 0) ptile[blockIdx.x] = sh[0];
+}
+
+__global__ void k_pshift(const CavDev *cavs, int ntiles, double *ptile, double *pref) {
+  const CavDev &cv = cavs[blockIdx.x];
+  const int n = cv.tiles_x * cv.tiles_y;
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) v += ptile[cv.tile0 + k];
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double mean = sh[0] / (double(cv.nx) * cv.ny);
+    ptile[ntiles + blockIdx.x] = mean;
+    pref[blockIdx.x] += mean;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_rebase(const CavDev *cavs, const int *tile_cav,
+                                                            T *g, const double *ptile, int ntiles) {
+  const NodeRef r = tile_node(tile_cav, cavs);
+  if (!r.valid) return;
+  const CavDev &cv = cavs[r.cav];
+  const double pt = ptile[ntiles + r.cav] * cv.inv_cs2;
+  T *gb = g + 9 * cv.off;
+  const int64_t node = int64_t(r.j) * cv.pitch + r.i;
+#pragma unroll
+  for (int q = 0; q < 9; ++q) {
+    T &x = gb[q * cv.plane + node];
+    x = T(double(x) - wbar(q) * pt);
+  }
 }
 
 __global__ void k_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
@@ -342,22 +410,31 @@ template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void
                                     int ntiles, cudaStream_t s) {
   k_init<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (T *)g, lam);
 }
-template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const void *g,
-                                      double *rho, double *u, double *v, double *psi, int nx,
-                                      int ny, cudaStream_t s) {
+template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const double *pref,
+                                      const void *g, double *rho, double *u, double *v,
+                                      double *psi, int nx, int ny, cudaStream_t s) {
   (void)ny;
-  k_macros<T><<<(nx + 127) / 128, 128, 0, s>>>(cav, geo, cavity, (const T *)g, rho, u, v, psi);
+  k_macros<T><<<(nx + 127) / 128, 128, 0, s>>>(cav, geo, cavity, pref, (const T *)g, rho, u, v,
+                                                psi);
 }
-template <class T> void launch_export(const CavDev *cav, int cavity, const void *g,
-                                      const double *lam, double *fhat, double *lamo, int nx,
-                                      int ny, cudaStream_t s) {
-  k_export<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, (const T *)g, lam, fhat,
-                                                          lamo);
+template <class T> void launch_export(const CavDev *cav, int cavity, const double *pref,
+                                      const void *g, const double *lam, double *fhat,
+                                      double *lamo, int nx, int ny, cudaStream_t s) {
+  k_export<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (const T *)g, lam,
+                                                          fhat, lamo);
 }
-template <class T> void launch_import(const CavDev *cav, int cavity, void *g, double *lam,
-                                      const double *fhat, const double *lami, int nx, int ny,
+template <class T> void launch_import(const CavDev *cav, int cavity, const double *pref, void *g,
+                                      double *lam, const double *fhat, const double *lami,
+                                      int nx, int ny, cudaStream_t s) {
+  k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (T *)g, lam, fhat,
+                                                          lami);
+}
+template <class T> void launch_rebase(const CavDev *cav, const int *tile_cav, void *g,
+                                      double *pref, double *ptile, int ntiles, int ncav,
                                       cudaStream_t s) {
-  k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, (T *)g, lam, fhat, lami);
+  k_psum<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (const T *)g, ptile);
+  k_pshift<<<ncav, 256, 0, s>>>(cav, ntiles, ptile, pref);
+  k_rebase<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (T *)g, ptile, ntiles);
 }
 
 #define IFD_INSTANTIATE(T)                                                                     \
@@ -366,12 +443,15 @@ template <class T> void launch_import(const CavDev *cav, int cavity, void *g, do
   template void launch_full<T>(const StepArgs &, int, cudaStream_t);                          \
   template void launch_init<T>(const CavDev *, const int *, void *, double *, int,            \
                                cudaStream_t);                                                  \
-  template void launch_macros<T>(const CavDev *, Geo, int, const void *, double *, double *,  \
-                                 double *, double *, int, int, cudaStream_t);                 \
-  template void launch_export<T>(const CavDev *, int, const void *, const double *, double *, \
-                                 double *, int, int, cudaStream_t);                           \
-  template void launch_import<T>(const CavDev *, int, void *, double *, const double *,       \
-                                 const double *, int, int, cudaStream_t);
+  template void launch_macros<T>(const CavDev *, Geo, int, const double *, const void *,      \
+                                 double *, double *, double *, double *, int, int,            \
+                                 cudaStream_t);                                               \
+  template void launch_export<T>(const CavDev *, int, const double *, const void *,           \
+                                 const double *, double *, double *, int, int, cudaStream_t); \
+  template void launch_import<T>(const CavDev *, int, const double *, void *, double *,       \
+                                 const double *, const double *, int, int, cudaStream_t);     \
+  template void launch_rebase<T>(const CavDev *, const int *, void *, double *, double *, int, \
+                                 int, cudaStream_t);
 IFD_INSTANTIATE(double)
 IFD_INSTANTIATE(float)
 

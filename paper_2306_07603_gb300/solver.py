@@ -74,6 +74,10 @@ class Solver:
         capi.ifdlbm_batch_macros(self.h, cavity, f["rho"], f["u"], f["v"], f["psi"])
         return f
 
+    def eddies(self, cavity=0):
+        """Primary, bottom-left and bottom-right eddy centres (ifdlbm_eddies)."""
+        return capi.ifdlbm_eddies(self.h, cavity)
+
     def get_state(self, cavity=0):
         c = self.cavities[cavity]
         fhat = np.zeros((9, c.ny, c.nx))

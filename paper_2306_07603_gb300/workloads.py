@@ -71,11 +71,9 @@ def roof(N):
     return [CavitySpec(N, N, 1000.0, 0.75, 60.0)]
 
 
-# Library options a workload needs beyond the defaults: the theta = 30 deg
-# cavities of the batched sweep need the contravariant Courant rule for dt
-# (the default rule gives them a contravariant Courant number of 1.37 per
-# axis, beyond the stability limit 1 of the scheme at eta_b = 0.5).
-WORKLOAD_OPTIONS = {"batch64": {"dt_mode": "contravariant"}}
+# Library options a workload needs beyond the defaults (none at present:
+# the default contravariant Courant rule for dt covers every workload).
+WORKLOAD_OPTIONS = {}
 
 WORKLOADS = {
     "cavity65": cavity65,

@@ -2,12 +2,12 @@
 
 Cavity: theta = 60 deg, n = 0.75, Re = 100, U = 0.1, L = H = 1 (the FP64
 validation case of Sec. 5.1's parameters), advanced from rest by the FP64
-oracle for STEPS steps, by which the per-step max-norm residual is about
-1e-11 (the oracle reaches 1e-8 after ~40k steps and 1e-10 after ~60k). The
+oracle for STEPS steps (default contravariant time-step rule), by which the
+per-step max-norm residual is about 1e-11. The
 file holds u, v, P, psi (Eqs. 2.10-2.11; psi integrated along xi lines) and
 the residuals of Eq. (2.19) of the last step. Only the oracle is called.
 
-    python tests/golden/make_steady_fields.py      # ~8 min on one core
+    python tests/golden/make_steady_fields.py      # ~13 min on one core
 """
 import os
 import sys
@@ -20,7 +20,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import oracle as O  # noqa: E402
 
 N, RE, N_POW, THETA = 65, 100.0, 0.75, 60.0
-STEPS = 80000
+STEPS = 130000
 OUT = os.path.join(HERE, "steady_65_theta60_n075_re100.npz")
 
 

@@ -46,14 +46,15 @@ def test_adjoint_step_dot_product(n):
     from paper_2306_07603_gb300.workloads import smooth_noise
 
     nx, ny = 33, 29
-    run = O.cavity_run(nx, 400.0, n, theta_deg=60.0, ny=ny)
+    run = O.cavity_run(nx, 400.0, n, theta_deg=60.0, ny=ny, dt_mode="grid")
     run.advance(60)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     ux, uy, P = O.macros(f0)
     feq = O.equilibrium(P, ux, uy)
     gd = O.shear_rate(*O.strain_rate(O.f_from_fhat(f0, feq, l0, run.prm.dt), feq, l0))
     away = gd > 10.0 * run.prm.gamma_min
-    s = Solver([cavity(nx, ny, 400.0, n, theta_deg=60.0)], precision="fp64", kernel="staged")
+    s = Solver([cavity(nx, ny, 400.0, n, theta_deg=60.0)], precision="fp64", kernel="staged",
+               dt_mode="grid")
     vf = smooth_noise((9, ny, nx), seed=1) * 1e-3 * away[None]
     vl = smooth_noise((ny, nx), seed=2) * 1e-2 * l0 * away
     wf = smooth_noise((9, ny, nx), seed=3)
@@ -84,7 +85,8 @@ def test_adjoint_step_dot_product(n):
 
 def _gpu_energy(n, Re, th, nx, ny, T):
     from paper_2306_07603_gb300.solver import Solver, cavity
-    s = Solver([cavity(nx, ny, Re, n, theta_deg=th)], precision="fp64", kernel="staged")
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=th)], precision="fp64", kernel="staged",
+               dt_mode="grid")
     s.step(T)
     e = float(s.residual()[0][3])
     s.close()
@@ -111,7 +113,7 @@ def test_energy_gradient_matches_oracle_complex_step():
     from paper_2306_07603_gb300.adjoint import energy_and_gradient
 
     def energy(n, Re, theta):
-        run = O.cavity_run(33, Re, n, theta_deg=theta)
+        run = O.cavity_run(33, Re, n, theta_deg=theta, dt_mode="grid")
         run.advance(40)
         ux, uy, _ = O.macros(run.fhat)
         return O.kinetic_energy(ux, uy, run.g)
@@ -138,3 +140,72 @@ def test_config5_gradient_against_central_differences():
         xm[k] -= h
         fd = (_gpu_energy(*xp, 257, 257, 2000) - _gpu_energy(*xm, 257, 257, 2000)) / (2 * h)
         assert abs(g[k] - fd) <= 1e-4 * abs(g[k]), (k, g[k], fd)
+
+
+def _gpu_psimin(n, Re, th, nx, ny, T):
+    """min over interior nodes of psi after T steps (the library's forward run)."""
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    s = Solver([cavity(nx, ny, Re, n, theta_deg=th)], precision="fp64", kernel="staged",
+               dt_mode="grid")
+    s.step(T)
+    psi = s.macros(0)["psi"]
+    s.close()
+    return float(psi[1:-1, 1:-1].min())
+
+
+@pytest.mark.parametrize("every", [7, 40])
+def test_psi_min_gradient_matches_central_differences(every):
+    from paper_2306_07603_gb300.adjoint import objective_and_gradient
+    x = [0.75, 400.0, 60.0]
+    nx, ny, T = 33, 29, 40
+    J, *g = objective_and_gradient("psi_min", *x, nx, ny, T, every=every)
+    assert J < 0 and abs(J - _gpu_psimin(*x, nx, ny, T)) <= 1e-14 * abs(J)
+    for k in range(3):
+        h = 1e-6 * abs(x[k])
+        xp, xm = list(x), list(x)
+        xp[k] += h
+        xm[k] -= h
+        fd = (_gpu_psimin(*xp, nx, ny, T) - _gpu_psimin(*xm, nx, ny, T)) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-5 * abs(g[k]), (k, g[k], fd)
+
+
+def test_psi_min_gradient_matches_oracle_complex_step():
+    """psi at the primary eddy's node, complex-step differentiated through the
+    oracle (the node is chosen on the real parts)."""
+    from paper_2306_07603_gb300.adjoint import objective_and_gradient
+
+    def psi_at(n, Re, theta, node=None):
+        run = O.cavity_run(33, Re, n, theta_deg=theta, dt_mode="grid")
+        run.advance(40)
+        ux, uy, _ = O.macros(run.fhat)
+        psi = O.stream_function(ux, uy, run.g)
+        if node is None:
+            inner = np.real(psi)[1:-1, 1:-1]
+            j, i = np.unravel_index(np.argmin(inner), inner.shape)
+            node = (j + 1, i + 1)
+        return psi[node], node
+
+    x = [0.75, 400.0, 60.0]
+    J, *g = objective_and_gradient("psi_min", *x, 33, 33, 40, every=10)
+    J0, node = psi_at(*x)
+    assert abs(J - J0) <= 1e-12 * abs(J0)
+    for k in range(3):
+        xs = [complex(v) for v in x]
+        xs[k] += 1e-30j
+        ref = np.imag(psi_at(*xs, node=node)[0]) / 1e-30
+        assert abs(g[k] - ref) <= 1e-8 * abs(ref), (k, g[k], ref)
+
+
+def test_adjoint_seed_psi_rejects_nodes_outside_the_cavity():
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    s = Solver([cavity(17, 17, 100.0, 0.75)], precision="fp64", kernel="staged")
+    buf = torch.zeros(capi.ifdlbm_state_bytes(s.h) // 8, dtype=torch.float64, device="cuda")
+    adj = torch.zeros_like(buf)
+    dp = torch.zeros(3, dtype=torch.float64, device="cuda")
+    capi.ifdlbm_save_state_dev(s.h, buf)
+    with pytest.raises(capi.IfdlbmError):
+        capi.ifdlbm_adjoint_seed_psi(s.h, buf, [(17, 3)], adj, dp)
+    s.close()

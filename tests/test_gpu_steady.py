@@ -5,14 +5,25 @@ case), advanced from rest for the number of steps stored with the oracle's
 fields (tests/golden/make_steady_fields.py calls only the oracle; the per-step
 max-norm residual there is ~1e-11). Bars:
 
-* FP64 (staged and fused): u, v, psi within 1e-12 of max|field|; P within
-  1e-12 of the magnitude of its Eq. (2.11) terms, c_s^2/|wbar_0| sum_{i>0} w_i
-  rho0 (P is a small difference of O(w_i) sums).
-* FP32 deviation storage (FP64 power law and reductions): u, v, P, psi within
-  1e-5 of max|field|.
+* FP64 (staged and fused): u, v, psi within 1e-12 of max|field|; P minus its
+  mean within 1e-12 of the magnitude of its Eq. (2.11) terms, c_s^2/|wbar_0|
+  sum_{i>0} w_i rho0 (P is a small difference of O(w_i) sums).
+* FP32 deviation storage (FP64 power law and reductions): u, v, psi and P
+  minus its mean within 1e-5 of max|field|, after FP32_STEPS steps. The
+  FP32 trajectory leaves the FP64 one during the transient and relaxes
+  towards its own steady state along the slowest cavity mode (time constant
+  ~44k steps at 65^2), so it is compared once that difference has levelled
+  off (measured: 7e-6 / 1.6e-5 / 1.8e-5 for u / v / psi at 130k steps,
+  2.4e-6 / 5.1e-6 / 5.4e-6 from 500k steps on).
 
-A steady state is an attractor of the step, so rounding differences do not
-grow along the run; the FP64 bar is the per-step bar.
+A steady velocity field is an attractor of the step, so rounding differences
+do not grow along the run and the FP64 bar is the per-step bar. The mean of P
+is not: a uniform pressure offset leaves f^eq's gradients, the advection and
+the wall rule unchanged, so it is a neutral mode, and the scheme (finite
+differences in non-conservative form, extrapolated walls) moves it at a
+constant rate once u is steady (oracle, 65^2: about -7.5e-7 per step). Its
+rounding differences add up over the run, so the mean is held to
+steps x (4 eps) x that magnitude, eps of the storage precision.
 """
 import os
 
@@ -24,6 +35,7 @@ import oracle as O
 pytestmark = pytest.mark.gpu
 
 GOLDEN = "steady_65_theta60_n075_re100.npz"
+FP32_STEPS = 500000
 KERNELS = {"staged": dict(kernel="staged"), "fused": dict(kernel="fused")}
 
 
@@ -62,7 +74,10 @@ def test_steady_fp64_fields_match_oracle(golden_dir, kname):
     for k in ("u", "v", "psi"):
         err = np.abs(m[k] - d[k]).max() / np.abs(d[k]).max()
         assert err <= 1e-12, (k, err)
-    assert np.abs(m["P"] - d["P"]).max() <= 1e-12 * _p_scale()
+    dP = (m["P"] - m["P"].mean()) - (d["P"] - d["P"].mean())
+    assert np.abs(dP).max() <= 1e-12 * _p_scale()
+    eps = np.finfo(np.float64).eps
+    assert abs(m["P"].mean() - d["P"].mean()) <= int(d["steps"]) * 4 * eps * _p_scale()
     # the last step's residuals (Eq. 2.19) are those of a converged run
     Eu, EP, Rinf = d["last_residual"]
     assert r[2] <= 10 * Rinf + 1e-13, (r[2], Rinf)
@@ -71,6 +86,10 @@ def test_steady_fp64_fields_match_oracle(golden_dir, kname):
 @pytest.mark.parametrize("kname", list(KERNELS))
 def test_steady_fp32_deviation_error(golden_dir, kname):
     d, case = _golden(golden_dir)
-    m, _ = _run(case, int(d["steps"]), precision="fp32dev", **KERNELS[kname])
-    errs = {k: np.abs(m[k] - d[k]).max() / np.abs(d[k]).max() for k in ("u", "v", "P", "psi")}
+    m, _ = _run(case, FP32_STEPS, precision="fp32dev", **KERNELS[kname])
+    errs = {k: np.abs(m[k] - d[k]).max() / np.abs(d[k]).max() for k in ("u", "v", "psi")}
+    pg, po = m["P"] - m["P"].mean(), d["P"] - d["P"].mean()
+    errs["P - mean"] = np.abs(pg - po).max() / np.abs(po).max()
     assert all(e <= 1e-5 for e in errs.values()), errs
+    eps = float(np.finfo(np.float32).eps)
+    assert abs(m["P"].mean() - d["P"].mean()) <= FP32_STEPS * 4 * eps * _p_scale()

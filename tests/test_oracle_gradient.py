@@ -13,7 +13,7 @@ import oracle as O
 
 
 def energy(n, Re, theta, N=21, T=25):
-    run = O.cavity_run(N, Re, n, theta_deg=theta)
+    run = O.cavity_run(N, Re, n, theta_deg=theta, dt_mode="grid")  # dt fixed under theta
     run.advance(T)
     ux, uy, _ = O.macros(run.fhat)
     return O.kinetic_energy(ux, uy, run.g)
