@@ -63,6 +63,11 @@ def parse_args(argv=None):
                    help="skip the adjoint measurement (257^2, 2000 steps, checkpoints every 100)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="CPU work budget of the oracle baseline sample")
+    p.add_argument("--fused-threads", type=int, default=0,
+                   help="fix the fused kernel's CTA width (64/128/256) and skip the autotuner")
+    p.add_argument("--fused-rows", type=int, default=0, help="rows per task with --fused-threads")
+    p.add_argument("--schedule", default="grid", choices=["grid", "static", "dynamic"],
+                   help="schedule with --fused-threads")
     return p.parse_args(argv)
 
 
@@ -237,7 +242,7 @@ def tuning_options(tuning):
                 schedule=names[tuning.schedule])
 
 
-def one_by_one_mlups(specs, precision, kernel, workload, steps, tuning):
+def one_by_one_mlups(specs, precision, kernel, workload, steps, layout):
     """The same cavities as separate handles, stepped one after another each
     time step (one launch per cavity instead of one per batch)."""
     import torch
@@ -245,8 +250,7 @@ def one_by_one_mlups(specs, precision, kernel, workload, steps, tuning):
     from paper_2306_07603_gb300 import capi
 
     stream = torch.cuda.Stream()
-    extra = tuning_options(tuning) if tuning is not None else {}
-    solvers = [make_solver([sp], precision, kernel, stream=stream, workload=workload, **extra)
+    solvers = [make_solver([sp], precision, kernel, stream=stream, workload=workload, **layout)
                for sp in specs]
     for s in solvers:
         s.step(3)
@@ -291,10 +295,14 @@ def run_ours(args):
     specs = WORKLOADS[args.workload]()
     lu_step = sum(s.nodes for s in specs)
 
-    s = make_solver(specs, args.precision, args.kernel, workload=args.workload)
+    fixed = {}
+    if args.fused_threads:
+        fixed = dict(fused_threads=args.fused_threads, fused_rows=args.fused_rows,
+                     schedule=args.schedule)
+    s = make_solver(specs, args.precision, args.kernel, workload=args.workload, **fixed)
     stream = s.stream
     tuning = None
-    if capi.ifdlbm_info(s.h, 0).fused_threads:
+    if capi.ifdlbm_info(s.h, 0).fused_threads and not fixed:
         tuning = s.autotune(trial_steps=10)           # layout and schedule, state unchanged
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sampler = ClockSampler(local)
@@ -353,15 +361,16 @@ def run_ours(args):
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
 
+    layout = fixed or (tuning_options(tuning) if tuning is not None else {})
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, specs, stream, world, tuning)
+        e2e = run_e2e(args, specs, stream, world, layout)
     batch = None
     if len(specs) > 1 and rank == 0:
         batch = {"cavities": len(specs), "batched_mlups": None,
                  "one_by_one_mlups": round(one_by_one_mlups(specs, args.precision, args.kernel,
                                                             args.workload, max(5, args.steps // 4),
-                                                            tuning), 2)}
+                                                            layout), 2)}
 
     out = None
     if rank == 0:
@@ -393,6 +402,8 @@ def run_ours(args):
             "e2e": e2e,
             "last_residual_cavity0": [float(x) for x in resid[0]],
         }
+        if fixed:
+            out["config"]["fused_layout"] = fixed
         if tuning is not None:
             out["config"]["autotuned"] = {"fused_threads": tuning.fused_threads,
                                           "fused_rows": tuning.fused_rows,
@@ -452,7 +463,7 @@ def run_adjoint_measure(nx=257, ny=257, T=2000, every=100, n=0.75, Re=400.0, the
             "J": float(J.detach())}
 
 
-def run_e2e(args, specs, stream, world, tuning=None):
+def run_e2e(args, specs, stream, world, layout=None):
     """Same metric through the public API with HOST buffers: create the batch
     from host parameters, then every step reads its residual back into pinned
     host memory (a device -> host copy and a synchronisation per step), and
@@ -468,8 +479,8 @@ def run_e2e(args, specs, stream, world, tuning=None):
     fields = [torch.empty((4, sp.ny, sp.nx), dtype=torch.float64, pin_memory=True) for sp in specs]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    extra = tuning_options(tuning) if tuning is not None else {}
-    s = make_solver(specs, args.precision, args.kernel, stream=stream, workload=args.workload, **extra)
+    s = make_solver(specs, args.precision, args.kernel, stream=stream, workload=args.workload,
+                    **(layout or {}))
     for _ in range(nsteps):
         capi.ifdlbm_step(s.h, 1)
         capi.ifdlbm_batch_residual(s.h, pinned.numpy())

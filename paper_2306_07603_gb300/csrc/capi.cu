@@ -190,13 +190,12 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.status = h->b.status;
     f.powtab = h->b.powtab;
     f.pref = h->b.pref;
+    f.cav_done = h->b.cav_done;
+    f.resid = h->b.resid;
     f.want_residual = want_residual ? 1 : 0;
     if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
+    // the residual of Eq. (2.19) is reduced inside the launch by each cavity's last task
     timed(h, IFDLBM_KPROF_FUSED, [&] { ifd::launch_fused<T>(f, h->fused_nt, h->grid, h->stream); });
-    if (want_residual)
-      timed(h, IFDLBM_KPROF_REDUCE, [&] {
-        ifd::launch_residual_reduce(h->b.cav, h->b.part, h->b.resid, h->ncav, h->stream);
-      });
     return;
   }
   ifd::StepArgs a{};
@@ -233,8 +232,8 @@ void enqueue_step_any(ifdlbm_ctx *h, int parity, bool want_residual) {
 }
 
 int launches_per_step(const ifdlbm_ctx *h, bool residual) {
-  const int base = h->kernel == IFDLBM_KERNEL_FUSED ? 1 : 3;
-  return residual ? base + 1 : base;
+  if (h->kernel == IFDLBM_KERNEL_FUSED) return 1;  // residual reduced inside the launch
+  return residual ? 4 : 3;
 }
 
 int ensure_graph(ifdlbm_ctx *h, int parity) {
@@ -575,6 +574,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   ok &= (h->stage = (double *)A(size_t(10 * h->max_n2) * sizeof(double))) != nullptr;
   ok &= (h->b.powtab = (double *)A(ifd::POW_TABLE_SIZE * sizeof(double))) != nullptr;
   ok &= (h->b.pref = (double *)A(size_t(ncav) * sizeof(double))) != nullptr;
+  ok &= (h->b.cav_done = (int *)A(size_t(ncav) * sizeof(int))) != nullptr;
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
   if (!ok) {
     release_all(h);
@@ -645,6 +645,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.pref, 0, size_t(ncav) * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.cav_done, 0, size_t(ncav) * sizeof(int), s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(h->b.ptile, 0, size_t(h->ntiles + ncav) * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.g[0], 0, 9 * off * tsize, s);

@@ -460,6 +460,21 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     p.du2max = double(leaf.du2max);
     p.u2max = double(leaf.u2max);
     block_partial<NT / 32>(p, a.part, ti);
+    // The last task of the cavity to finish reduces the cavity's partials
+    // (a counter, no waiting: every other CTA just moves on).
+    __shared__ int last;
+    __syncthreads();                       // this task's partial is written
+    if (threadIdx.x == 0) {
+      __threadfence();                     // ... and visible device-wide
+      last = atomicAdd(&a.cav_done[task.cav], 1) == cv.nparts - 1;
+    }
+    __syncthreads();
+    if (last) {
+      __threadfence();                     // see the other tasks' partials
+      reduce_partials_block<NT / 32>(a.part + int64_t(cv.part0) * NPART, cv.nparts,
+                                     a.resid + 4 * task.cav);
+      if (threadIdx.x == 0) a.cav_done[task.cav] = 0;   // re-armed for the next step
+    }
   }
   __syncthreads();  // the next task reuses the shared rings
 }

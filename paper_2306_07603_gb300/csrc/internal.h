@@ -60,6 +60,7 @@ struct Bufs {
   Geo geo;
   double *powtab;    // tables of pow_fast (fastpow.cuh)
   double *pref;      // [ncav] reference pressure: f-hat = w rho0 + wbar pref / c_s^2 + g
+  int *cav_done;     // [ncav] fused kernel: tasks finished in the current step
   double *ptile;     // [ntiles + ncav] scratch of the re-basing reduction
 };
 
@@ -102,6 +103,8 @@ struct FusedArgs {
   unsigned *status;
   const double *powtab;
   const double *pref;  // [ncav] reference pressure of the stored deviations
+  int *cav_done;       // [ncav] tasks of the step finished (zero between steps)
+  double *resid;       // [ncav][4] residual outputs (formed by each cavity's last task)
   int want_residual;
 };
 

@@ -96,4 +96,45 @@ __device__ __forceinline__ void reduce_partials(const double *part, int nslots, 
   }
 }
 
+// The same reduction by one block of NWARPS warps (any 32-multiple size):
+// each thread sums a fixed stride of slots, then a fixed shuffle tree and a
+// fixed pass over the warps, so that the result depends only on nslots and
+// the block size.
+template <int NWARPS>
+__device__ __forceinline__ void reduce_partials_block(const double *part, int nslots, double *out) {
+  __shared__ double sh[NWARPS][7];
+  const int t = threadIdx.x, w = t >> 5, l = t & 31;
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  for (int s = t; s < nslots; s += NWARPS * 32) {
+    const double *pp = part + int64_t(s) * NPART;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) acc[k] += pp[k];
+    acc[5] = fmax(acc[5], pp[5]);
+    acc[6] = fmax(acc[6], pp[6]);
+  }
+#pragma unroll
+  for (int k = 0; k < 5; ++k) acc[k] = warp_sum(acc[k]);
+  acc[5] = warp_max(acc[5]);
+  acc[6] = warp_max(acc[6]);
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < 7; ++k) sh[w][k] = acc[k];
+  __syncthreads();
+  if (t == 0) {
+    double r[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) r[k] = sh[0][k];
+    for (int q = 1; q < NWARPS; ++q) {
+#pragma unroll
+      for (int k = 0; k < 5; ++k) r[k] += sh[q][k];
+      r[5] = fmax(r[5], sh[q][5]);
+      r[6] = fmax(r[6], sh[q][6]);
+    }
+    out[0] = sqrt(r[0]) / sqrt(r[1]);  // E(u), Eq. (2.19)
+    out[1] = sqrt(r[2]) / sqrt(r[3]);  // E(P), Eq. (2.19)
+    out[2] = sqrt(r[5]) / sqrt(r[6]);  // max-norm velocity residual
+    out[3] = r[4];                     // kinetic energy, Eq. (5.1)
+  }
+}
+
 }  // namespace ifd
