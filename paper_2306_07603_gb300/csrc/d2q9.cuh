@@ -146,8 +146,7 @@ __device__ __forceinline__ double cxi_of(int q, double A, double B) {
 
 // Wall-node rule (Sec. 4): F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
 template <class T>
-__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
-  const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
+__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, T c, T cs2, T ics2) {
   T ux, uy, P;
   moments(F, c, cs2, ux, uy, P);
   T fw[9], fn[9];
@@ -155,6 +154,10 @@ __device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
   equilibrium(P, ux, uy, c, ics2, fn);
 #pragma unroll
   for (int q = 0; q < 9; ++q) F[q] = fw[q] + (F[q] - fn[q]);
+}
+template <class T>
+__device__ __forceinline__ void nee(T F[9], T uwx, T uwy, const CavDev &cv) {
+  nee(F, uwx, uwy, T(cv.c), T(cv.cs2), T(cv.inv_cs2));
 }
 
 }  // namespace ifd

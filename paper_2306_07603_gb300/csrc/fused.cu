@@ -42,6 +42,7 @@ namespace ifd {
 namespace {
 
 constexpr int PF = 5;     // per-thread row slots: prefetched state, then f-hat^+
+constexpr int LEAF = 16;  // rows per leaf sum of the residual terms
 constexpr int RING = 6;   // rows of the f-bar^+ and f(t+dt/2) rings
 
 template <class T, int NT>
@@ -55,23 +56,6 @@ struct FusedSmem {
 };
 
 __device__ __forceinline__ int slot6(int r) { return (r + 12) % RING; }
-
-// c xi_x of row j and the Jacobian x_xi H: FP64 metrics for FP64 arithmetic,
-// their rounded float copies for FP32 arithmetic.
-template <class T>
-__device__ __forceinline__ T row_cxix(const Geo &g, const CavDev &cv, int j) {
-  if constexpr (sizeof(T) == 8)
-    return cv.c * g.xix[cv.goff + j];
-  else
-    return g.cxix_f[cv.goff + j];
-}
-template <class T>
-__device__ __forceinline__ T row_jac(const Geo &g, const CavDev &cv, int j) {
-  if constexpr (sizeof(T) == 8)
-    return g.xxi[cv.goff + j] * cv.H;
-  else
-    return g.jac_f[cv.goff + j];
-}
 
 __device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
@@ -147,8 +131,8 @@ struct AdvectAll {
   }
 };
 
-// Residual terms of one node, summed over up to 8 rows in T before they are
-// added to the FP64 partials (a leaf sum; every sum beyond it is FP64).
+// Residual terms of one node, summed over up to LEAF rows in T before they
+// are added to the FP64 partials (a leaf sum; every sum beyond it is FP64).
 template <class T>
 struct Leaf {
   T du2 = 0, u2 = 0, dP2 = 0, P2 = 0, ek = 0;
@@ -183,7 +167,7 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
   l.ek += T(0.5) * wJ * u2;
   l.du2max = max(l.du2max, du2);
   l.u2max = max(l.u2max, u2);
-  if (++l.n == 8) leaf_flush(l, p);
+  if (++l.n == LEAF) leaf_flush(l, p);
 }
 
 }  // namespace
@@ -194,7 +178,28 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const Task task = a.tasks[ti];
   const CavDev &cv = a.cav[task.cav];
   const int i0 = task.i0, i1 = task.i1, j0 = task.j0, j1 = task.j1;
-  const int nx = cv.nx, ny = cv.ny;
+  // Everything the march needs from the cavity descriptor, read once: the
+  // descriptor is in global memory, and the march's stores could alias it
+  // as far as the compiler knows.
+  const int nx = cv.nx, ny = cv.ny, pitch = cv.pitch;
+  const int64_t plane = cv.plane, goff = cv.goff;
+  const double cvc = cv.c, cvH = cv.H;
+  const T Uw = T(cv.U);
+  const int part0 = cv.part0, nparts = cv.nparts;
+  // c xi_x of row j and the Jacobian x_xi H: FP64 metrics for FP64
+  // arithmetic, their rounded float copies for FP32 arithmetic.
+  auto row_cxix = [&](int j) -> T {
+    if constexpr (sizeof(T) == 8)
+      return cvc * a.geo.xix[goff + j];
+    else
+      return a.geo.cxix_f[goff + j];
+  };
+  auto row_jac = [&](int j) -> T {
+    if constexpr (sizeof(T) == 8)
+      return a.geo.xxi[goff + j] * cvH;
+    else
+      return a.geo.jac_f[goff + j];
+  };
   const int t = threadIdx.x;
   const int h = t / NC;                              // row parity of this thread (warp-uniform)
   const int l = t - h * NC;                          // column lane
@@ -218,7 +223,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T eta_b = T(cv.eta_b);
   const T i2dxi = T(cv.inv2dxi), i2deta = T(cv.inv2deta);
   const T ceta_unit = T(cv.c / cv.H);
-  const T xeH = T(a.geo.xeH[cv.goff + cc]);          // x_eta / H of this column
+  const T xeH = T(a.geo.xeH[goff + cc]);             // x_eta / H of this column
   const T wx = T(((c == 0 || c == nx - 1) ? 0.5 : 1.0) * cv.dxi);
   const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
@@ -235,18 +240,20 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     const int r = row_of(it);
     if (r >= rlo && r <= rhi) {
       const int s = it % PF;
-      const int64_t node = int64_t(r) * cv.pitch + cc;
+      const int64_t node = int64_t(r) * pitch + cc;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) cp_async(&S.sf[s][q][t], gin + q * cv.plane + node, sizeof(T));
+      for (int q = 0; q < 9; ++q) cp_async(&S.sf[s][q][t], gin + q * plane + node, sizeof(T));
     }
     cp_commit();
   };
   // lambda_prev of a row Step (2) works on, loaded one iteration ahead
   auto lam_load = [&](int r) {
-    return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * cv.pitch + cc] : 0.0;
+    return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * pitch + cc] : 0.0;
   };
   // per-cavity constants of the relaxation time
   const double gmin2 = cv.gmin2, half_nm1 = cv.half_nm1, Kics2 = cv.Kics2;
+  // largest float not above gamma_min^2 (so that every clamped q is >= it)
+  const float gmin2_f = __double2float_rd(gmin2);
   const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
   // Step (2) for this thread's row of iteration `it`: moments, f^eq and
   // lambda(t). The row of iteration it + 1 is formed during the full step of
@@ -273,8 +280,15 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as relaxation_time)
     const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
-    double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
-    q = q > gmin2 ? q : gmin2;
+    double q;
+    if constexpr (sizeof(T) == 4) {
+      // the strain rate is FP32 here: clamp before widening (one FP32 max
+      // instead of an FP64 compare), with the clamp as the float below gamma_min^2
+      q = double(fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f));
+    } else {
+      q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+      q = q > gmin2 ? q : gmin2;
+    }
     o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     return o;
   };
@@ -294,6 +308,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   if (in_a(row_of(0))) take(collide(0, lam_load(row_of(0))));
   double lp_next = lam_load(row_of(1));  // lambda_prev of the next row
   T Lprev = T(0);                        // lambda(t) of this thread's previous row
+  // metrics of this iteration's half-step and full-step rows, loaded one
+  // iteration ahead (rows clamped into the cavity; unused outside it)
+  auto crow = [&](int r) { return min(max(r, 0), ny - 1); };
+  T A1 = row_cxix(crow(kb - 2 + h)), A2 = row_cxix(crow(kb - 4 + h)), J2 = row_jac(crow(kb - 4 + h));
 
   for (int it = 0; it < nit; ++it) {
     const int k = kb + 2 * it;
@@ -303,7 +321,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     T Lcur = T(0);
     if (in_a(ar)) {
       const int s = it % PF, sb = slot6(ar);
-      if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * cv.pitch + c] = nlam;
+      if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * pitch + c] = nlam;
       const T L = T(nlam);
       Lcur = L;
       const T i2 = T(1) / (T(2) * L + dt);
@@ -331,7 +349,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     const bool do1 = m >= mlo && m <= mhi;
     if (do1 && inner_c && l >= 2 && l < NC - 2) {
       const int sm = slot6(m);
-      const T A = row_cxix<T>(a.geo, cv, m);           // c xi_x
+      const T A = A1;                                  // c xi_x of row m
       const T B = A * xeH;                             // c xi_x x_eta / H
       const bool lo = m == 1, hi = m == ny - 2;
       T fbar[9];
@@ -360,7 +378,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         T F[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) F[q] = S.fh[slot6(m)][q][ln];
-        nee(F, T(0), T(0), cv);
+        nee(F, T(0), T(0), c_, cs2, ics2);
 #pragma unroll
         for (int q = 0; q < 9; ++q) S.fh[slot6(m)][q][l] = F[q];
       }
@@ -371,7 +389,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         T F[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) F[q] = S.fh[src][q][ln];
-        nee(F, (lid && inner_c) ? T(cv.U) : T(0), T(0), cv);
+        nee(F, (lid && inner_c) ? Uw : T(0), T(0), c_, cs2, ics2);
 #pragma unroll
         for (int q = 0; q < 9; ++q) S.fh[dst][q][l] = F[q];
       }
@@ -386,7 +404,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     T gnv[9];
     if (do2 && inner_c && l >= 4 && l < NC - 4) {
       const int so = slot6(o);
-      const T A = row_cxix<T>(a.geo, cv, o);
+      const T A = A2;                                  // c xi_x of row o
       const T B = A * xeH;
       const bool lo = o == 1, hi = o == ny - 2;
       gnv[0] = S.sf[sp][0][t];
@@ -403,6 +421,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     }
     if (in_a(row_of(it + 1))) take(collide(it + 1, lp_next));  // lambda of the next row
     lp_next = lam_load(row_of(it + 2));
+    const T J2o = J2;                                // Jacobian of row o
+    A1 = row_cxix(crow(m + 2));
+    A2 = row_cxix(crow(o + 2));
+    J2 = row_jac(crow(o + 2));
     __syncthreads();  // f-hat(t + dt) of columns 1 and nx-2
 
     if (do2 && own) {
@@ -410,11 +432,11 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         const int side = c == 0 ? 0 : 1;
 #pragma unroll
         for (int q = 0; q < 9; ++q) gnv[q] = S.gw[h][side][q];
-        nee(gnv, T(0), T(0), cv);
+        nee(gnv, T(0), T(0), c_, cs2, ics2);
       }
-      const int64_t node = int64_t(o) * cv.pitch + c;
+      const int64_t node = int64_t(o) * pitch + c;
 #pragma unroll
-      for (int q = 0; q < 9; ++q) gout[q * cv.plane + node] = gnv[q];
+      for (int q = 0; q < 9; ++q) gout[q * plane + node] = gnv[q];
       if (a.want_residual) {
         T ux, uy, P, u0, v0, P0;
         moments(gnv, c_, cs2, ux, uy, P);
@@ -422,7 +444,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 #pragma unroll
         for (int q = 0; q < 9; ++q) fpo[q] = S.sf[sp][q][t];
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
-        const T wJ = wx * wy_in * row_jac<T>(a.geo, cv, o);
+        const T wJ = wx * wy_in * J2o;
         leaf_add(leaf, p, ux, uy, P, u0, v0, P0, Pr, wJ, a.status);
       }
       // wall rows produced with their neighbour rows
@@ -438,16 +460,16 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 #pragma unroll
           for (int q = 0; q < 9; ++q) F[q] = gnv[q];
         }
-        nee(F, (top && inner_c) ? T(cv.U) : T(0), T(0), cv);
+        nee(F, (top && inner_c) ? Uw : T(0), T(0), c_, cs2, ics2);
         const int r = bottom ? 0 : ny - 1;
-        const int64_t nd = int64_t(r) * cv.pitch + c;
+        const int64_t nd = int64_t(r) * pitch + c;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) gout[q * cv.plane + nd] = F[q];
+        for (int q = 0; q < 9; ++q) gout[q * plane + nd] = F[q];
         if (a.want_residual) {
           T wx2, wy2, wP2;
           moments(F, c_, cs2, wx2, wy2, wP2);
           const int e = bottom ? 0 : 1;
-          const T wJ = wx * wy_edge * row_jac<T>(a.geo, cv, r);
+          const T wJ = wx * wy_edge * row_jac(r);
           leaf_add(leaf, p, wx2, wy2, wP2, S.edge[e][0][l], S.edge[e][1][l], S.edge[e][2][l], Pr,
                    wJ, a.status);
         }
@@ -466,12 +488,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     __syncthreads();                       // this task's partial is written
     if (threadIdx.x == 0) {
       __threadfence();                     // ... and visible device-wide
-      last = atomicAdd(&a.cav_done[task.cav], 1) == cv.nparts - 1;
+      last = atomicAdd(&a.cav_done[task.cav], 1) == nparts - 1;
     }
     __syncthreads();
     if (last) {
       __threadfence();                     // see the other tasks' partials
-      reduce_partials_block<NT / 32>(a.part + int64_t(cv.part0) * NPART, cv.nparts,
+      reduce_partials_block<NT / 32>(a.part + int64_t(part0) * NPART, nparts,
                                      a.resid + 4 * task.cav);
       if (threadIdx.x == 0) a.cav_done[task.cav] = 0;   // re-armed for the next step
     }
