@@ -181,12 +181,14 @@ def kernel_source_digest(kernel="fused"):
     return h.hexdigest()[:16]
 
 
-def traffic_per_launch(kernel, precision, lu_per_launch):
+def traffic_per_launch(kernel, precision, lu_per_launch, workload=None):
+    """DRAM bytes per launch from the ncu record of this kernel (and workload,
+    where one was captured: an L2-resident workload moves fewer bytes)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d[f"{kernel}:{precision}"]
+        e = d.get(f"{kernel}:{precision}:{workload}") or d[f"{kernel}:{precision}"]
         if e.get("src_digest") != kernel_source_digest(kernel):
             return None
         return float(e["bytes_per_lu"]) * lu_per_launch
@@ -356,7 +358,7 @@ def run_ours(args):
         achieved = algo / per_launch_s / 1e9
         roofline = {"bound": "hbm", "kernel": DEVICE_KERNEL[dom], "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic_per_launch(dom, args.precision, lu_step),
+                    "traffic": traffic_per_launch(dom, args.precision, lu_step, args.workload),
                     "algorithmic_bytes": algo, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
