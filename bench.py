@@ -181,6 +181,18 @@ def kernel_source_digest(kernel="fused"):
     return h.hexdigest()[:16]
 
 
+def profile_record(kernel, precision, workload=None):
+    """The ncu record of this kernel (and workload) if its sources are unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(f"{kernel}:{precision}:{workload}") or d[f"{kernel}:{precision}"]
+        return e if e.get("src_digest") == kernel_source_digest(kernel) else None
+    except Exception:
+        return None
+
+
 def traffic_per_launch(kernel, precision, lu_per_launch, workload=None):
     """DRAM bytes per launch from the ncu record of this kernel (and workload,
     where one was captured: an L2-resident workload moves fewer bytes)."""
@@ -363,6 +375,14 @@ def run_ours(args):
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
 
+    # the FP64 pipe, which bounds the fused step before HBM does (power law of
+    # Eq. 1.4 in FP64 at 1/64 of the FP32 rate): its utilisation from ncu
+    rec = profile_record(dom, args.precision, args.workload) if dom is not None else None
+    fp64 = None
+    if rec is not None and "fp64_pipe_pct_elapsed" in rec:
+        fp64 = {"bound": "alu", "unit": "fraction of the FP64 pipe's peak issue rate",
+                "frac": round(rec["fp64_pipe_pct_elapsed"] / 100.0, 3),
+                "source": rec["source"] + " (ncu sm__inst_executed_pipe_fp64, elapsed)"}
     layout = fixed or (tuning_options(tuning) if tuning is not None else {})
     e2e = None
     if not args.no_e2e:
@@ -398,6 +418,7 @@ def run_ours(args):
                        "baseline_metric": BASELINE_METRIC},
             "hbm_gbs_algorithmic": round(value * 1e6 * (88 if args.precision == "fp32dev" else 160) / 1e9, 1),
             "roofline": roofline,
+            "roofline_fp64": fp64,
             "kernels_ms_per_launch": {k: round(v[0] / v[1], 5) for k, v in kern.items()},
             "gpu_launches": launches_all,
             "clocks": clocks,
