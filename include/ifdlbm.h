@@ -231,6 +231,21 @@ int ifdlbm_get_state(ifdlbm_handle h, int cavity, double *fhat, double *lambda_p
  * compares against these fields. Synchronises. */
 int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const double *lambda_prev);
 
+/* Time series without synchronising (unsteady runs, Sec. 5.3: probe
+ * velocities and the kinetic energy of Eq. 5.1 over time). Both enqueue on
+ * the handle's stream and return at once; results are valid once the stream
+ * reaches them.
+ *  ifdlbm_residual_dev: copies the [ncav][4] array of ifdlbm_batch_residual
+ *    (E(u), E(P), max-norm residual, kinetic energy of the last step that
+ *    formed them) into the DEVICE array out.
+ *  ifdlbm_probe_dev: for n >= 0 probes, DEVICE int array probes[n][3] =
+ *    (cavity, i, j), writes the DEVICE double array out[n][3] = (u, v, P) of
+ *    Eqs. 2.10-2.11 at node (i, j) of that cavity at the current state (P is
+ *    the pressure of Eq. 2.11, rho = rho0 + P / c_s^2). A probe outside its
+ *    cavity yields NaNs; the probe array is read on the device only. */
+int ifdlbm_residual_dev(ifdlbm_handle h, double *out);
+int ifdlbm_probe_dev(ifdlbm_handle h, int n, const int *probes, double *out);
+
 /* Copies of the whole batch state between the handle and caller-owned
  * DEVICE memory of ifdlbm_state_bytes(h) bytes (opaque layout, valid only
  * for the same handle). Used for checkpoints. Do not synchronise. */

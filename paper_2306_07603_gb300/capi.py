@@ -97,6 +97,8 @@ _SIGS = {
     "ifdlbm_batch_macros": (C.c_int, [_H, C.c_int, _P, _P, _P, _P]),
     "ifdlbm_macros_dev": (C.c_int, [_H, C.c_int, _P, _P, _P, _P]),
     "ifdlbm_residual": (C.c_int, [_H, _P]),
+    "ifdlbm_residual_dev": (C.c_int, [_H, _P]),
+    "ifdlbm_probe_dev": (C.c_int, [_H, C.c_int, _P, _P]),
     "ifdlbm_batch_residual": (C.c_int, [_H, _P]),
     "ifdlbm_get_state": (C.c_int, [_H, C.c_int, _P, _P]),
     "ifdlbm_set_state": (C.c_int, [_H, C.c_int, _P, _P]),
@@ -240,6 +242,16 @@ def ifdlbm_macros_dev(h, cavity, rho=None, u=None, v=None, psi=None):
 
 def ifdlbm_residual(h, out):
     return _check(load_library().ifdlbm_residual(h, _ptr(out)), h)
+
+
+def ifdlbm_residual_dev(h, out):
+    return _check(load_library().ifdlbm_residual_dev(h, _ptr(out)), h)
+
+
+def ifdlbm_probe_dev(h, probes, out):
+    """probes: CUDA int32 tensor [n][3] of (cavity, i, j); out: CUDA float64 tensor [n][3]."""
+    return _check(load_library().ifdlbm_probe_dev(h, int(probes.shape[0]), _ptr(probes),
+                                                  _ptr(out)), h)
 
 
 def ifdlbm_batch_residual(h, out):

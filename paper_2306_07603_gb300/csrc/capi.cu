@@ -788,6 +788,32 @@ int ifdlbm_batch_residual(ifdlbm_handle h, double *out) {
   return check_status(h);
 }
 
+int ifdlbm_residual_dev(ifdlbm_handle h, double *out) {
+  if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaMemcpyAsync(out, h->b.resid, size_t(h->ncav) * 4 * sizeof(double),
+                                  cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "residual_dev copy");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_probe_dev(ifdlbm_handle h, int n, const int *probes, double *out) {
+  if (!h || n < 0 || (n > 0 && (!probes || !out)))
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle, count or arrays");
+  if (n == 0) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  if (h->precision == IFDLBM_FP64)
+    ifd::launch_probe<double>(h->b.cav, h->ncav, h->b.pref, h->b.g[h->cur], n, probes, out,
+                              h->stream);
+  else
+    ifd::launch_probe<float>(h->b.cav, h->ncav, h->b.pref, h->b.g[h->cur], n, probes, out,
+                             h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "probe launch");
+  return IFDLBM_OK;
+}
+
 int ifdlbm_residual(ifdlbm_handle h, double *out) {
   if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
   if (h->ncav == 1) return ifdlbm_batch_residual(h, out);

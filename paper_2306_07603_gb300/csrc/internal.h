@@ -162,6 +162,10 @@ template <class T> void launch_import(const CavDev *cav, int cavity, const doubl
                                       void *g, double *lam,
                                       const double *fhat, const double *lami, int nx, int ny,
                                       cudaStream_t s);
+// u, v, P at probe nodes [n][3] = (cavity, i, j) into out [n][3] (NaN for a
+// probe outside its cavity).
+template <class T> void launch_probe(const CavDev *cav, int ncav, const double *pref, const void *g,
+                                     int n, const int *probes, double *out, cudaStream_t s);
 // Re-bases the stored deviations of every cavity on its mean pressure:
 // shift = mean over the cavity's nodes of P(g), g_i -= wbar_i shift / c_s^2,
 // pref += shift (the state f-hat = w rho0 + wbar pref / c_s^2 + g is

@@ -278,6 +278,29 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *
   }
 }
 
+// Probes: u, v, P (Eqs. 2.10-2.11, P including the reference pressure of the
+// stored deviations) at n nodes given as (cavity, i, j); a probe outside its
+// cavity (or naming no cavity) gets NaN.
+template <class T>
+__global__ void k_probe(const CavDev *cavs, int ncav, const double *pref, const T *g, int n,
+                        const int *probes, double *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int c = probes[3 * k], i = probes[3 * k + 1], j = probes[3 * k + 2];
+  if (c < 0 || c >= ncav || i < 0 || j < 0 || i >= cavs[c].nx || j >= cavs[c].ny) {
+    out[3 * k] = out[3 * k + 1] = out[3 * k + 2] = nan("");
+    return;
+  }
+  const CavDev &cv = cavs[c];
+  T gg[9];
+  load9(g + 9 * cv.off, cv.plane, int64_t(j) * cv.pitch + i, gg);
+  T ux, uy, P;
+  moments(gg, T(cv.c), T(cv.cs2), ux, uy, P);
+  out[3 * k] = double(ux);
+  out[3 * k + 1] = double(uy);
+  out[3 * k + 2] = pref[c] + double(P);
+}
+
 template <class T>
 __global__ void k_export(const CavDev *cavs, int cavity, const double *pref, const T *g,
                          const double *lam, double *fhat, double *lamo) {
@@ -429,6 +452,10 @@ template <class T> void launch_import(const CavDev *cav, int cavity, const doubl
   k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (T *)g, lam, fhat,
                                                           lami);
 }
+template <class T> void launch_probe(const CavDev *cav, int ncav, const double *pref, const void *g,
+                                     int n, const int *probes, double *out, cudaStream_t s) {
+  k_probe<T><<<(n + 127) / 128, 128, 0, s>>>(cav, ncav, pref, (const T *)g, n, probes, out);
+}
 template <class T> void launch_rebase(const CavDev *cav, const int *tile_cav, void *g,
                                       double *pref, double *ptile, int ntiles, int ncav,
                                       cudaStream_t s) {
@@ -450,6 +477,8 @@ template <class T> void launch_rebase(const CavDev *cav, const int *tile_cav, vo
                                  const double *, double *, double *, int, int, cudaStream_t); \
   template void launch_import<T>(const CavDev *, int, const double *, void *, double *,       \
                                  const double *, const double *, int, int, cudaStream_t);     \
+  template void launch_probe<T>(const CavDev *, int, const double *, const void *, int,       \
+                                const int *, double *, cudaStream_t);                         \
   template void launch_rebase<T>(const CavDev *, const int *, void *, double *, double *, int, \
                                  int, cudaStream_t);
 IFD_INSTANTIATE(double)

@@ -1,0 +1,171 @@
+"""Unsteady cavity flows: probe and kinetic-energy time series and their statistics.
+
+Sec. 5.3 of the paper follows the velocity (u, v) at the cavity centre, the
+point (1.07735, 0.5) of the theta = 60 deg map (xi = eta = 0.5), and the
+kinetic energy E(t) of Eq. (5.1), and calls a flow steady, periodic,
+quasi-periodic or turbulent from the phase portrait of (u, v) and the power
+spectrum of E(t). This module records those series on the GPU without
+synchronising (``ifdlbm_probe_dev``, ``ifdlbm_residual_dev``, one sample every
+``every`` steps) and reduces them on the host:
+
+* mean and variance of E and of u, v at every probe;
+* the power spectrum of E(t) - mean (Hann window), its principal frequency
+  and period (in lattice time units, t = steps x dt), and its peaks;
+* a regime label. The paper gives the regimes by inspection only; the rule
+  used here (a reading): steady if the relative standard deviation of E over
+  the record is below ``steady_tol``; turbulent if less than ``concentration``
+  of the fluctuation power lies within two bins of the ``max_discrete``
+  strongest spectral peaks (a broadband spectrum); else periodic if every
+  peak above ``peak_frac`` of the largest lies within one bin of a multiple
+  of the principal frequency, and quasi-periodic if not.
+
+The arithmetic of the step runs in libifdlbm.so; only the statistics of the
+recorded series are formed here.
+
+    python -m paper_2306_07603_gb300.regimes --cases theta60     # Sec. 5.3, theta = 60 deg
+    python -m paper_2306_07603_gb300.regimes --case 257,60,1.5,4000 --precision fp64
+    python -m paper_2306_07603_gb300.regimes --workload unsteady1025
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from .workloads import WORKLOAD_OPTIONS, WORKLOADS, CavitySpec
+
+# Sec. 5.3, theta = 60 deg, 256^2 cells: the cases whose regime the paper states.
+THETA60 = [CavitySpec(257, 257, Re, n, 60.0) for n, Re in
+           ((1.5, 3000.0), (1.5, 4000.0), (1.5, 5000.0), (1.0, 2500.0), (1.0, 3000.0),
+            (1.0, 4000.0), (0.5, 750.0), (0.5, 1000.0), (0.5, 2000.0))]
+
+# probe points (xi, eta): the cavity centre first (the paper's probe), then the
+# four quarter points
+PROBES = ((0.5, 0.5), (0.25, 0.25), (0.75, 0.25), (0.25, 0.75), (0.75, 0.75))
+
+
+def record(specs, precision="fp32dev", transient=1_000_000, steps=1_000_000, every=100,
+           probes=PROBES, **opts):
+    """Advance all cavities `transient` steps, then record `steps` more, sampling
+    E(t) and u, v at the probe nodes every `every` steps."""
+    import torch
+
+    from . import capi
+    from .solver import Solver, cavity
+    s = Solver([cavity(c.nx, c.ny, c.Re, c.n, theta_deg=c.theta_deg, U_lid=c.U_lid, L=c.L, H=c.H)
+                for c in specs], precision=precision, **opts)
+    idx = [(k, int(round(xi * (c.nx - 1))), int(round(eta * (c.ny - 1))))
+           for k, c in enumerate(specs) for (xi, eta) in probes]
+    nsamp = steps // every
+    with torch.cuda.stream(s.stream):
+        pidx = torch.tensor(idx, dtype=torch.int32, device="cuda")
+        pbuf = torch.empty((nsamp, len(idx), 3), dtype=torch.float64, device="cuda")
+        rbuf = torch.empty((nsamp, len(specs), 4), dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    done = 0
+    while done < transient:
+        k = min(100_000, transient - done)
+        s.step(k)
+        done += k
+    for m in range(nsamp):
+        s.step(every)
+        capi.ifdlbm_probe_dev(s.h, pidx, pbuf[m])
+        capi.ifdlbm_residual_dev(s.h, rbuf[m])
+    s.sync()
+    wall = time.time() - t0
+    dts = [capi.ifdlbm_info(s.h, k).dt for k in range(len(specs))]
+    out = {"probes": pbuf.cpu().numpy().reshape(nsamp, len(specs), len(probes), 3),
+           "energy": rbuf.cpu().numpy()[:, :, 3], "dt": dts, "every": every,
+           "transient": transient, "steps": steps, "seconds": wall,
+           "lattice_updates": sum(c.nodes for c in specs) * (transient + steps)}
+    s.close()
+    return out
+
+
+def spectrum(x, dt_sample):
+    """One-sided power spectrum of x - mean with a Hann window."""
+    y = (x - x.mean()) * np.hanning(len(x))
+    p = np.abs(np.fft.rfft(y)) ** 2
+    f = np.fft.rfftfreq(len(x), d=dt_sample)
+    return f, p
+
+
+def classify(E, dt_sample, steady_tol=1e-6, peak_frac=0.01, max_discrete=12, concentration=0.8):
+    """Regime of an energy series (see the module docstring) and its spectrum facts."""
+    mean, std = float(E.mean()), float(E.std())
+    if std <= steady_tol * abs(mean):
+        return {"regime": "steady", "rel_std": std / abs(mean), "f0": None, "period": None,
+                "peaks": [], "concentration": None}
+    f, p = spectrum(E, dt_sample)
+    p[0] = 0.0
+    df = f[1] - f[0]
+    k0 = int(np.argmax(p))
+    f0 = float(f[k0])
+    # local maxima above peak_frac of the largest, strongest first
+    pk = sorted((k for k in range(1, len(p) - 1)
+                 if p[k] >= peak_frac * p[k0] and p[k] >= p[k - 1] and p[k] >= p[k + 1]),
+                key=lambda k: -p[k])
+    near = np.zeros(len(p), dtype=bool)
+    for k in pk[:max_discrete]:
+        near[max(k - 2, 0):k + 3] = True
+    conc = float(p[near].sum() / p.sum())
+    if conc < concentration:
+        regime = "turbulent"
+    elif all(round(f[k] / f0) >= 1 and abs(f[k] - round(f[k] / f0) * f0) <= df for k in pk):
+        regime = "periodic"
+    else:
+        regime = "quasi-periodic"
+    return {"regime": regime, "rel_std": std / abs(mean), "f0": f0,
+            "period": 1.0 / f0 if f0 > 0 else None,
+            "peaks": [float(f[k]) for k in pk[:8]], "concentration": conc}
+
+
+def summarize(specs, rec, probes=PROBES, **kw):
+    rows = []
+    for k, c in enumerate(specs):
+        dts = rec["dt"][k] * rec["every"]
+        E = rec["energy"][:, k]
+        cl = classify(E, dts, **kw)
+        pr = rec["probes"][:, k]
+        rows.append({
+            "grid": f"{c.nx}x{c.ny}", "theta": c.theta_deg, "n": c.n, "Re": c.Re,
+            "E_mean": float(E.mean()), "E_var": float(E.var()), **cl,
+            "probes": [{"xi": xi, "eta": eta, "u_mean": float(pr[:, q, 0].mean()),
+                        "u_var": float(pr[:, q, 0].var()), "v_mean": float(pr[:, q, 1].mean()),
+                        "v_var": float(pr[:, q, 1].var())}
+                       for q, (xi, eta) in enumerate(probes)]})
+    return rows
+
+
+def main(argv=None):
+    p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    p.add_argument("--cases", choices=["theta60"], default=None)
+    p.add_argument("--workload", choices=sorted(WORKLOADS), default=None)
+    p.add_argument("--case", default=None, help="one cavity: N,theta_deg,n,Re (e.g. 257,60,1.5,4000)")
+    p.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp64"])
+    p.add_argument("--transient", type=int, default=1_000_000)
+    p.add_argument("--steps", type=int, default=1_000_000)
+    p.add_argument("--every", type=int, default=100)
+    p.add_argument("--save", default=None, help="write the raw series to this .npz")
+    a = p.parse_args(argv)
+    if a.case:
+        N, th, n, Re = (float(v) for v in a.case.split(","))
+        specs, opts = [CavitySpec(int(N), int(N), Re, n, th)], {}
+    elif a.workload:
+        specs, opts = WORKLOADS[a.workload](), dict(WORKLOAD_OPTIONS.get(a.workload, {}))
+    else:
+        specs, opts = THETA60, {}
+    rec = record(specs, a.precision, a.transient, a.steps, a.every, **opts)
+    if a.save:
+        np.savez_compressed(a.save, probes=rec["probes"], energy=rec["energy"],
+                            dt=np.array(rec["dt"]), every=a.every)
+    print(json.dumps({"precision": a.precision, "transient": a.transient, "steps": a.steps,
+                      "every": a.every, "seconds": round(rec["seconds"], 1),
+                      "mlups": round(rec["lattice_updates"] / rec["seconds"] / 1e6, 1),
+                      "cases": summarize(specs, rec)}))
+
+
+if __name__ == "__main__":
+    main()

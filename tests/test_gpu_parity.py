@@ -342,3 +342,32 @@ def test_fp32_rebasing_keeps_the_state():
     assert np.array_equal(fc, fa)
     s.close()
     t.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32dev"])
+def test_probes_and_device_residual_match_the_host_outputs(precision):
+    """ifdlbm_probe_dev gives u, v and P of ifdlbm_macros at the probe nodes
+    (NaN outside the cavity); ifdlbm_residual_dev copies the residual array."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    specs = [(41, 37, 400.0, 0.75, 60.0), (33, 29, 100.0, 1.5, 45.0)]
+    s = solver([cav(*sp) for sp in specs], precision=precision)
+    s.step(1500)                       # FP32: past one re-basing of the pressure reference
+    probes = [(0, 20, 18), (0, 0, 36), (1, 32, 0), (1, 7, 11), (1, 33, 5), (2, 1, 1)]
+    idx = torch.tensor(probes, dtype=torch.int32, device="cuda")
+    out = torch.zeros((len(probes), 3), dtype=torch.float64, device="cuda")
+    res = torch.zeros((2, 4), dtype=torch.float64, device="cuda")
+    capi.ifdlbm_probe_dev(s.h, idx, out)
+    capi.ifdlbm_residual_dev(s.h, res)
+    s.sync()
+    out, res = out.cpu().numpy(), res.cpu().numpy()
+    m = [s.macros(k) for k in range(2)]
+    for k, (c, i, j) in enumerate(probes):
+        if c > 1 or i >= specs[c][0] or j >= specs[c][1]:
+            assert np.all(np.isnan(out[k]))
+            continue
+        assert out[k, 0] == m[c]["u"][j, i] and out[k, 1] == m[c]["v"][j, i]
+        assert abs(1.0 + 3.0 * out[k, 2] - m[c]["rho"][j, i]) <= 1e-15
+    assert np.array_equal(res, np.array(s.residual()))
+    s.close()
