@@ -12,12 +12,16 @@ synchronising (``ifdlbm_probe_dev``, ``ifdlbm_residual_dev``, one sample every
 * the power spectrum of E(t) - mean (Hann window), its principal frequency
   and period (in lattice time units, t = steps x dt), and its peaks;
 * a regime label. The paper gives the regimes by inspection only; the rule
-  used here (a reading): steady if the relative standard deviation of E over
-  the record is below ``steady_tol``; turbulent if less than ``concentration``
-  of the fluctuation power lies within two bins of the ``max_discrete``
-  strongest spectral peaks (a broadband spectrum); else periodic if every
-  peak above ``peak_frac`` of the largest lies within one bin of a multiple
-  of the principal frequency, and quasi-periodic if not.
+  used here (a reading) works on E(t) minus its linear trend over the record:
+  steady if its relative standard deviation is below ``steady_tol``;
+  drifting (the record is too short to tell: the flow is still settling) if
+  the strongest spectral peak lies in the lowest ``drift_bins`` bins;
+  turbulent if less than ``concentration`` of the fluctuation power lies
+  within two bins of the ``max_discrete`` strongest peaks (a broadband
+  spectrum); else periodic if every peak above ``peak_frac`` of the largest
+  lies within one bin of a multiple of the principal frequency, and
+  quasi-periodic if not. The relative drift of E over the record is
+  reported beside the label.
 
 The arithmetic of the step runs in libifdlbm.so; only the statistics of the
 recorded series are formed here.
@@ -92,13 +96,20 @@ def spectrum(x, dt_sample):
     return f, p
 
 
-def classify(E, dt_sample, steady_tol=1e-6, peak_frac=0.01, max_discrete=12, concentration=0.8):
+def classify(E, dt_sample, steady_tol=1e-6, peak_frac=0.01, max_discrete=12, concentration=0.8,
+             drift_bins=3):
     """Regime of an energy series (see the module docstring) and its spectrum facts."""
-    mean, std = float(E.mean()), float(E.std())
+    E = np.asarray(E, dtype=float)
+    t = np.arange(len(E), dtype=float)
+    slope, icpt = np.polyfit(t, E, 1)
+    r = E - (slope * t + icpt)
+    mean, std = float(E.mean()), float(r.std())
+    drift = float(slope * (len(E) - 1) / mean)
+    facts = {"rel_std": std / abs(mean), "drift": drift}
     if std <= steady_tol * abs(mean):
-        return {"regime": "steady", "rel_std": std / abs(mean), "f0": None, "period": None,
-                "peaks": [], "concentration": None}
-    f, p = spectrum(E, dt_sample)
+        return {"regime": "steady", **facts, "f0": None, "period": None, "peaks": [],
+                "concentration": None}
+    f, p = spectrum(r, dt_sample)
     p[0] = 0.0
     df = f[1] - f[0]
     k0 = int(np.argmax(p))
@@ -111,14 +122,15 @@ def classify(E, dt_sample, steady_tol=1e-6, peak_frac=0.01, max_discrete=12, con
     for k in pk[:max_discrete]:
         near[max(k - 2, 0):k + 3] = True
     conc = float(p[near].sum() / p.sum())
-    if conc < concentration:
+    if k0 <= drift_bins:
+        regime = "drifting"
+    elif conc < concentration:
         regime = "turbulent"
     elif all(round(f[k] / f0) >= 1 and abs(f[k] - round(f[k] / f0) * f0) <= df for k in pk):
         regime = "periodic"
     else:
         regime = "quasi-periodic"
-    return {"regime": regime, "rel_std": std / abs(mean), "f0": f0,
-            "period": 1.0 / f0 if f0 > 0 else None,
+    return {"regime": regime, **facts, "f0": f0, "period": 1.0 / f0 if f0 > 0 else None,
             "peaks": [float(f[k]) for k in pk[:8]], "concentration": conc}
 
 

@@ -38,6 +38,16 @@ def test_broadband_series_is_turbulent():
     assert c["regime"] == "turbulent" and c["concentration"] < 0.8
 
 
+def test_trend_is_removed_and_slow_settling_is_drifting():
+    f0 = 0.37
+    E = 1.0 + 0.001 * T + 0.01 * np.sin(2 * np.pi * f0 * T)
+    c = classify(E, DT)
+    assert c["regime"] == "periodic" and abs(c["f0"] - f0) <= 1.0 / (len(T) * DT)
+    E = 1.0 + 0.05 * np.exp(-T / 400.0)          # still settling over the record
+    c = classify(E, DT)
+    assert c["regime"] == "drifting" and c["drift"] < 0
+
+
 def test_spectrum_peak_at_the_signal_frequency():
     f, p = spectrum(np.sin(2 * np.pi * 1.25 * T), DT)
     assert abs(f[np.argmax(p)] - 1.25) <= 1.0 / (len(T) * DT)
