@@ -161,6 +161,9 @@ def main(argv=None):
     p.add_argument("--steps", type=int, default=1_000_000)
     p.add_argument("--every", type=int, default=100)
     p.add_argument("--save", default=None, help="write the raw series to this .npz")
+    p.add_argument("--eta-b", type=float, default=None, help="blend of Eq. 2.5 (default 0.5)")
+    p.add_argument("--only", default=None,
+                   help="with --cases: comma-separated indices of the cases to run")
     a = p.parse_args(argv)
     if a.case:
         N, th, n, Re = (float(v) for v in a.case.split(","))
@@ -169,11 +172,16 @@ def main(argv=None):
         specs, opts = WORKLOADS[a.workload](), dict(WORKLOAD_OPTIONS.get(a.workload, {}))
     else:
         specs, opts = THETA60, {}
+        if a.only:
+            specs = [specs[int(k)] for k in a.only.split(",")]
+    if a.eta_b is not None:
+        opts["eta_b"] = a.eta_b
     rec = record(specs, a.precision, a.transient, a.steps, a.every, **opts)
     if a.save:
         np.savez_compressed(a.save, probes=rec["probes"], energy=rec["energy"],
                             dt=np.array(rec["dt"]), every=a.every)
-    print(json.dumps({"precision": a.precision, "transient": a.transient, "steps": a.steps,
+    print(json.dumps({"precision": a.precision, "eta_b": opts.get("eta_b", 0.5),
+                      "transient": a.transient, "steps": a.steps,
                       "every": a.every, "seconds": round(rec["seconds"], 1),
                       "mlups": round(rec["lattice_updates"] / rec["seconds"] / 1e6, 1),
                       "cases": summarize(specs, rec)}))
