@@ -188,6 +188,42 @@ def relaxation_time(gdot, K, n, gamma_min, c=1.0):
     return K * g ** (n - 1.0) / sound_speed_sq(c)
 
 
+def relaxation_time_implicit(fhat, feq, dt, K, n, gamma_min, c=1.0, iters=200):
+    """lam solving lam = K max(gamma-dot(lam), gamma_min)^(n-1) / c_s^2 node by node.
+
+    The implicit form of Eq. (2.14), which the paper lags (the text after
+    Eq. 2.14 takes the strain rate with the previous step's lam). With f from
+    f-hat by Eq. (2.18) at the same lam, f^ne = 2 lam / (2 lam + dt) (f-hat -
+    f^eq), and Eqs. (2.12)-(2.13) give gamma-dot(lam) = a / (2 lam + dt),
+    a = 2 sqrt((Pi_xx^2 + 2 Pi_xy^2 + Pi_yy^2) / 2) / c_s^2 with
+    Pi = sum_i c_i c_i (f-hat_i - f^eq_i), which does not depend on lam.
+    F(lam) = lam - K max(gamma-dot(lam), gamma_min)^(n-1) / c_s^2 increases
+    strictly with lam, is negative at lam = 0 and non-negative at
+    lam_hi = K/c_s^2 max over gamma in [gamma_min, max(a/dt, gamma_min)] of
+    gamma^(n-1); its root is found by bisection (real arithmetic only).
+    """
+    cs2 = sound_speed_sq(c)
+    d = fhat - feq
+    ex, ey = _bcast(EX * c, d[0]), _bcast(EY * c, d[0])
+    pxx, pxy, pyy = (np.sum(w * d, axis=0) for w in (ex * ex, ex * ey, ey * ey))
+    a = 2.0 * np.sqrt(0.5 * (pxx * pxx + 2.0 * pxy * pxy + pyy * pyy)) / cs2
+    C = K / cs2
+    gmax = np.maximum(a / dt, gamma_min)
+    lo = np.zeros_like(a)
+    hi = C * np.maximum(gmax ** (n - 1.0), gamma_min ** (n - 1.0))
+
+    def F(lam):
+        g = np.maximum(a / (2.0 * lam + dt), gamma_min)
+        return lam - C * g ** (n - 1.0)
+
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        pos = F(mid) >= 0.0
+        hi = np.where(pos, mid, hi)
+        lo = np.where(pos, lo, mid)
+    return 0.5 * (lo + hi)
+
+
 # ---------------------------------------------------------------------------
 # Geometry: isosceles trapezoid mapped to the unit square, Eqs. (3.1)-(3.8)
 # ---------------------------------------------------------------------------
@@ -343,6 +379,7 @@ class Params:
     eta_b: float
     rho0: float = 1.0
     c: float = 1.0
+    implicit_lambda: bool = False   # solve Eq. (2.14) at the current lam instead of lagging
 
 
 def cavity_grid(nx, ny, L=1.0, H=1.0, theta_deg=60.0, U=0.1, c=1.0):
@@ -391,7 +428,8 @@ def periodic_grid(nx, ny, Lx=1.0, Ly=1.0, periodic_eta=True, c=1.0):
 
 
 def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None,
-                  gamma_min=None, dt=None, dt_mode="contravariant", grid=None):
+                  gamma_min=None, dt=None, dt_mode="contravariant", grid=None,
+                  implicit_lambda=False):
     """Parameters of a cavity run.
 
     * K from Re, Eq. (2.15.1).
@@ -409,6 +447,8 @@ def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None
     * READING (blend): eta_b, which the paper leaves free in [0, 1], defaults
       to DEFAULT_ETA_B.
     * READING (zero-shear clamp): gamma_min defaults to 1e-3 U / H.
+    * implicit_lambda: solve Eq. (2.14) with the strain rate of the current
+      lam (relaxation_time_implicit) instead of the paper's lagged lam.
     """
     K = consistency_coefficient(Re, n, U, H)
     if dt is None and dt_mode == "contravariant":
@@ -423,7 +463,8 @@ def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None
         eta_b = DEFAULT_ETA_B
     if gamma_min is None:
         gamma_min = 1e-3 * U / H
-    return Params(dt=dt, K=K, n=n, gamma_min=gamma_min, eta_b=eta_b, c=c)
+    return Params(dt=dt, K=K, n=n, gamma_min=gamma_min, eta_b=eta_b, c=c,
+                  implicit_lambda=implicit_lambda)
 
 
 DEFAULT_ETA_B = 0.5
@@ -548,6 +589,8 @@ def step(fhat, lam_prev, g: Grid, prm: Params, return_stages=False):
     Sxx, Sxy, Syy = strain_rate(f, feq, lam_prev, c)       # Eqs. (2.12)-(2.13)
     gdot = shear_rate(Sxx, Sxy, Syy)                       # Eq. (1.4)
     lam = relaxation_time(gdot, prm.K, prm.n, prm.gamma_min, c)  # Eq. (2.14)
+    if prm.implicit_lambda:                                # Eq. (2.14) at the current lam
+        lam = relaxation_time_implicit(fhat, feq, dt, prm.K, prm.n, prm.gamma_min, c)
 
     # Step (3): f-hat^+
     fhp = fhat_plus(fhat, feq, lam, dt)                    # Eq. (2.15)
