@@ -91,6 +91,7 @@ typedef struct {
   int fused_rows;    /* FUSED: rows per CTA task (>= 2); 0 = automatic */
   int schedule;      /* FUSED: IFDLBM_SCHED_*; default GRID */
   int dt_mode;       /* IFDLBM_DT_*: how dt follows from cfl when dt <= 0 */
+  int lambda_mode;   /* IFDLBM_LAMBDA_*: how Eq. (2.14) meets the strain rate */
 } ifdlbm_options;
 
 /* Time-step rules ("c = 1, CFL = 0.5", Sec. 5.1). */
@@ -101,6 +102,17 @@ typedef struct {
 #define IFDLBM_DT_CONTRAVARIANT 1 /* dt = cfl * min(dxi / max|c_xi|, deta / max|c_eta|),
                                      the Courant number of the contravariant speeds
                                      of Eq. (3.4) (default); equal to GRID at 90 deg */
+
+/* Relaxation time of Step (2). The paper lags it (text after Eq. 2.14): the
+ * strain rate of Eqs. (2.12)-(2.13) is taken with the previous step's lambda.
+ * The implicit form solves lambda = K max(gamma-dot(lambda), gamma_min)^(n-1)
+ * / c_s^2 at every node, gamma-dot(lambda) = a / (2 lambda + dt) with a from
+ * sum_i c_i c_i (f-hat_i - f^eq_i) (Eq. 2.18 at the same lambda), by a
+ * bracketed Newton iteration in FP64 (the root is unique: the residual
+ * increases strictly with lambda). Both forms share steady states. The
+ * adjoint needs the lagged form. */
+#define IFDLBM_LAMBDA_LAGGED 0   /* default */
+#define IFDLBM_LAMBDA_IMPLICIT 1
 
 /* Cavity-to-CTA schedules of the fused kernel. Tasks are strips of columns x
  * segments of rows of every cavity of the batch. */

@@ -191,6 +191,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.powtab = h->b.powtab;
     f.pref = h->b.pref;
     f.cav_done = h->b.cav_done;
+    f.implicit = h->opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
     f.resid = h->b.resid;
     f.want_residual = want_residual ? 1 : 0;
     if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
@@ -374,6 +375,7 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   opt->fused_rows = 0;
   opt->schedule = IFDLBM_SCHED_GRID;
   opt->dt_mode = IFDLBM_DT_CONTRAVARIANT;
+  opt->lambda_mode = IFDLBM_LAMBDA_LAGGED;
   return IFDLBM_OK;
 }
 
@@ -401,6 +403,8 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_threads must be 0, 64, 128 or 256");
   if (opt.dt_mode != IFDLBM_DT_GRID && opt.dt_mode != IFDLBM_DT_CONTRAVARIANT)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown dt_mode");
+  if (opt.lambda_mode != IFDLBM_LAMBDA_LAGGED && opt.lambda_mode != IFDLBM_LAMBDA_IMPLICIT)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown lambda_mode");
   if (opt.schedule < IFDLBM_SCHED_GRID || opt.schedule > IFDLBM_SCHED_DYNAMIC)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown schedule");
   if (opt.fused_rows < 0 || opt.fused_rows == 1)
@@ -469,6 +473,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     cv.inv_cs2 = 1.0 / cv.cs2;
     cv.K = std::pow(s.U_lid, 2.0 - s.n) * std::pow(H, s.n) / s.Re;  // Eq. (2.15.1)
     cv.nm1 = s.n - 1.0;
+    cv.implicit = opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
     if (opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_CONTRAVARIANT) {
@@ -958,6 +963,8 @@ namespace {
 int adjoint_ready(ifdlbm_ctx *h) {
   if (h->precision != IFDLBM_FP64 || h->kernel != IFDLBM_KERNEL_STAGED)
     return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: needs a FP64 handle with the staged kernels");
+  if (h->opt.lambda_mode != IFDLBM_LAMBDA_LAGGED)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the lagged relaxation time");
   if (h->adj_g1) return IFDLBM_OK;
   const size_t P = size_t(h->total_plane) * sizeof(double);
   bool ok = true;

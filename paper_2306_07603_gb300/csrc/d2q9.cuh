@@ -91,6 +91,48 @@ __device__ __forceinline__ T toward(T F, T feq, T b) {
   return F + b * (feq - F);
 }
 
+// Implicit form of Eq. (2.14): lam = C max(a / (2 lam + dt), gamma_min)^(n-1)
+// with C = K / c_s^2 and a = 2 sqrt((Pxx^2 + 2 Pxy^2 + Pyy^2) / 2) / c_s^2,
+// Pxx.. the second moments of f-hat - f^eq (Eq. 2.18 at the same lam turns
+// them into gamma-dot(lam) = a / (2 lam + dt)). F(lam) = lam - C max(...)^(n-1)
+// increases strictly, so the root is unique: it is the clamp value
+// lam_c = C gamma_min^(n-1) when gamma-dot(lam_c) <= gamma_min, and otherwise
+// lies in [0, lam_c] (n < 1) or [lam_c, C (a/dt)^(n-1)] (n > 1) with
+// gamma-dot > gamma_min. Newton from lam_start, kept inside the bracket by
+// bisection, one FP64 power per iteration; it stops once the Newton step is
+// below 4e-15 of lam (F = lam - P is itself a difference of nearly equal
+// numbers, so steps much smaller than that are rounding). Kept out of line so
+// that the lagged path is compiled as without it.
+static __device__ __noinline__ double lambda_implicit(double a, double lam_start, const CavDev &cv,
+                                                      const double *powtab) {
+  const double C = cv.Kics2, dt = cv.dt, m = cv.nm1, lamc = cv.lam0;
+  if (m == 0.0) return C;
+  if (a <= cv.gmin * (2.0 * lamc + dt)) return lamc;
+  double lo, hi;
+  if (m < 0.0) {
+    lo = 0.0;
+    hi = lamc;
+  } else {
+    lo = lamc;
+    hi = C * pow_fast((a / dt) * (a / dt), cv.half_nm1, powtab);
+  }
+  double lam = (lam_start > lo && lam_start < hi) ? lam_start : 0.5 * (lo + hi);
+  for (int it = 0; it < 20; ++it) {
+    const double x = 2.0 * lam + dt;
+    const double g = a / x;
+    const double P = C * pow_fast(g * g, cv.half_nm1, powtab);
+    const double F = lam - P;
+    if (F == 0.0) break;                                   // the root itself
+    if (F > 0.0) hi = lam; else lo = lam;
+    double next = lam - F / (1.0 + 2.0 * m * P / x);
+    if (!(next >= lo && next <= hi)) next = 0.5 * (lo + hi);
+    const bool done = fabs(next - lam) <= 4e-15 * next;
+    lam = next;
+    if (done) break;
+  }
+  return lam;
+}
+
 // Relaxation time of Step (2): strain rate from f^ne (Eqs. 2.12-2.13, with
 // f = f(f-hat, lam_prev) of Eq. 2.18), q = |gamma-dot|^2 = 2 D:D, the
 // clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) evaluated as
@@ -100,6 +142,10 @@ __device__ __forceinline__ T toward(T F, T feq, T b) {
 template <class T>
 __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
                                                   const CavDev &cv, const double *powtab) {
+  if (cv.implicit) {
+    const T G2 = T(0.5) * (Pxx * Pxx + T(2) * Pxy * Pxy + Pyy * Pyy);
+    return lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, powtab);
+  }
   // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
   const T k = T(-2) / ((T(2) * T(lam_prev) + T(cv.dt)) * T(cv.cs2));
   const T Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;

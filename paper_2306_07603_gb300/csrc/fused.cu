@@ -172,7 +172,7 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 
 }  // namespace
 
-template <class T, int NT>
+template <class T, int NT, bool IMPL>
 __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
   constexpr int NC = NT / 2;
   const Task task = a.tasks[ti];
@@ -277,6 +277,11 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     for (int q = 0; q < 9; ++q) d[q] = g[q] - o.geq[q];
     T pxx, pxy, pyy;
     second_moments(d, c_, pxx, pxy, pyy);
+    if constexpr (IMPL) {                                  // implicit form of Eq. (2.14)
+      const T G2 = T(0.5) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy);
+      o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
+      return o;
+    }
     // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as relaxation_time)
     const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
@@ -512,13 +517,13 @@ struct Occ {
 // blockIdx.x, blockIdx.x + gridDim.x, ... of the largest-first order;
 // 2 persistent CTAs taking positions from an atomic counter (no waiting on
 // other CTAs: a CTA that finds the list exhausted returns).
-template <class T, int NT>
+template <class T, int NT, bool IMPL>
 __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
   __shared__ int next;
   if (a.schedule == 0) {
-    fused_task<T, NT>(a, S, blockIdx.x);
+    fused_task<T, NT, IMPL>(a, S, blockIdx.x);
     return;
   }
   for (int it = 0;; ++it) {
@@ -532,15 +537,15 @@ __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
       __syncthreads();
     }
     if (pos >= a.ntasks) return;
-    fused_task<T, NT>(a, S, a.order[pos]);
+    fused_task<T, NT, IMPL>(a, S, a.order[pos]);
   }
 }
 
-template <class T, int NT>
+template <class T, int NT, bool IMPL>
 static void configure_nt() {
   static bool configured = false;  // the attribute is per function
   if (!configured) {
-    cudaFuncSetAttribute(k_fused<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fused<T, NT, IMPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(FusedSmem<T, NT>)));
     configured = true;
   }
@@ -548,15 +553,20 @@ static void configure_nt() {
 
 template <class T, int NT>
 static void launch_fused_nt(const FusedArgs &a, int grid, cudaStream_t s) {
-  configure_nt<T, NT>();
-  k_fused<T, NT><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+  if (a.implicit) {
+    configure_nt<T, NT, true>();
+    k_fused<T, NT, true><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+  } else {
+    configure_nt<T, NT, false>();
+    k_fused<T, NT, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+  }
 }
 
 template <class T, int NT>
 static int blocks_per_sm_nt() {
-  configure_nt<T, NT>();
+  configure_nt<T, NT, false>();
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT>, NT,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false>, NT,
                                                 int(sizeof(FusedSmem<T, NT>)));
   return n;
 }

@@ -30,6 +30,8 @@ struct CavDev {
   double dcot;              // d cot(theta) / d theta_deg (adjoint)
   double lnHU;              // ln H - ln U: d ln K / d n (adjoint)
   double Re;                // Reynolds number (adjoint)
+  int implicit;             // 1: lambda from the implicit form of Eq. (2.14), 0: lagged
+  int pad_;
 };
 
 // 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
@@ -104,6 +106,7 @@ struct FusedArgs {
   const double *powtab;
   const double *pref;  // [ncav] reference pressure of the stored deviations
   int *cav_done;       // [ncav] tasks of the step finished (zero between steps)
+  int implicit;        // 1: implicit form of Eq. (2.14) (kernel variant), 0: lagged
   double *resid;       // [ncav][4] residual outputs (formed by each cavity's last task)
   int want_residual;
 };

@@ -371,3 +371,66 @@ def test_probes_and_device_residual_match_the_host_outputs(precision):
         assert abs(1.0 + 3.0 * out[k, 2] - m[c]["rho"][j, i]) <= 1e-15
     assert np.array_equal(res, np.array(s.residual()))
     s.close()
+
+
+IMPLICIT_CASES = [(67, 45, 100.0, 0.75, 60.0, 40), (33, 29, 1000.0, 0.5, 45.0, 30),
+                  (41, 37, 400.0, 1.5, 75.0, 30), (35, 33, 100.0, 1.0, 30.0, 30)]
+
+
+@pytest.mark.parametrize("kname", ["staged", "fused64x8", "fused256x16"])
+@pytest.mark.parametrize("nx,ny,Re,n,th,k0", IMPLICIT_CASES)
+def test_implicit_lambda_one_step_fp64_parity(nx, ny, Re, n, th, k0, kname):
+    """lambda_mode 'implicit' (Eq. 2.14 at the current lambda; the oracle
+    bisects, the library runs a bracketed Newton iteration): one step from an
+    oracle state. lambda is held pointwise to 1e-12 max|lambda| plus
+    |n - 1| lambda da / a, da = 32 eps max|f-hat| / c_s^2 the rounding of a
+    (it is formed from f-hat - f^eq, a difference of O(w_i) numbers)."""
+    run = oracle_run(nx, ny, Re, n, th)
+    run.advance(k0)
+    f0, l0 = run.fhat.copy(), run.lam.copy()
+    prm = O.cavity_params(nx, ny, Re, n, grid=run.g, implicit_lambda=True)
+    fo, lo = O.step(f0, l0, run.g, prm)
+    s = solver([cav(nx, ny, Re, n, th)], lambda_mode="implicit", **KERNELS[kname])
+    s.set_state(0, f0, l0)
+    s.step(1)
+    fg, lg = s.get_state(0)
+    ux, uy, P = O.macros(f0)
+    feq = O.equilibrium(P, ux, uy)
+    d = f0 - feq
+    pxx = (O.EX[:, None, None] ** 2 * d).sum(0)
+    pxy = (O.EX[:, None, None] * O.EY[:, None, None] * d).sum(0)
+    pyy = (O.EY[:, None, None] ** 2 * d).sum(0)
+    a = 6.0 * np.sqrt(0.5 * (pxx ** 2 + 2 * pxy ** 2 + pyy ** 2))
+    da = 32 * np.finfo(float).eps * np.abs(f0).max() * 3.0
+    lam_tol = TOL64 * np.abs(lo).max() + abs(n - 1.0) * lo * da / np.maximum(a, 1e-300)
+    compare_state(fg, lg, fo, lo, lam_tol=lam_tol)
+
+
+def test_implicit_lambda_fp32_one_step_error():
+    run = oracle_run(67, 45, 100.0, 0.75, 60.0)
+    run.advance(200)
+    f0, l0 = run.fhat.copy(), run.lam.copy()
+    prm = O.cavity_params(67, 45, 100.0, 0.75, grid=run.g, implicit_lambda=True)
+    fo, lo = O.step(f0, l0, run.g, prm)
+    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev", lambda_mode="implicit")
+    s.set_state(0, f0, l0)
+    s.step(1)
+    fg, lg = s.get_state(0)
+    ug, vg, Pg = O.macros(fg)
+    uo, vo, Po = O.macros(fo)
+    assert rel(ug, uo) < 1e-5 and rel(vg, vo) < 1e-5 and rel(Pg, Po) < 1e-4
+    assert rel(lg, lo) < 1e-5
+
+
+def test_adjoint_rejects_the_implicit_form():
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    s = solver([cav(17, 17, 100.0, 0.75, 60.0)], precision="fp64", kernel="staged",
+               lambda_mode="implicit")
+    buf = torch.zeros(capi.ifdlbm_state_bytes(s.h) // 8, dtype=torch.float64, device="cuda")
+    dp = torch.zeros(3, dtype=torch.float64, device="cuda")
+    capi.ifdlbm_save_state_dev(s.h, buf)
+    with pytest.raises(capi.IfdlbmError):
+        capi.ifdlbm_adjoint_seed_energy(s.h, buf, torch.zeros_like(buf), dp)
+    s.close()
