@@ -405,6 +405,66 @@ def cavity_grid(nx, ny, L=1.0, H=1.0, theta_deg=60.0, U=0.1, c=1.0):
                 y_eta=met["y_eta"] + 0.0 * (xi + eta), wall_u=wall_u, x=x, y=y)
 
 
+def quad_xy(xi, eta, corners):
+    """Bilinear (Coons) map of the unit square onto the quadrilateral with
+    corners ((x0, y0) bottom-left, (x1, y1) bottom-right, (x2, y2) top-left,
+    (x3, y3) top-right): xi runs along the bottom and lid, eta up the sides."""
+    (x0, y0), (x1, y1), (x2, y2), (x3, y3) = corners
+    w = ((1 - xi) * (1 - eta), xi * (1 - eta), (1 - xi) * eta, xi * eta)
+    x = w[0] * x0 + w[1] * x1 + w[2] * x2 + w[3] * x3
+    y = w[0] * y0 + w[1] * y1 + w[2] * y2 + w[3] * y3
+    return x, y
+
+
+def quad_metrics(xi, eta, corners):
+    """Analytic derivatives of the bilinear map, the Jacobian (Eq. 3.3) and the
+    inverse metrics (Eq. 3.2); eta_x need not vanish here."""
+    (x0, y0), (x1, y1), (x2, y2), (x3, y3) = corners
+    x_xi = (1 - eta) * (x1 - x0) + eta * (x3 - x2) + 0.0 * xi
+    y_xi = (1 - eta) * (y1 - y0) + eta * (y3 - y2) + 0.0 * xi
+    x_eta = (1 - xi) * (x2 - x0) + xi * (x3 - x1) + 0.0 * eta
+    y_eta = (1 - xi) * (y2 - y0) + xi * (y3 - y1) + 0.0 * eta
+    return inverse_metrics(x_xi, x_eta, y_xi, y_eta)
+
+
+def quad_grid(nx, ny, corners, U=0.1, c=1.0):
+    """A lid-driven cavity on a general convex quadrilateral (per-node metrics).
+
+    READING (the paper's cavities are trapezoids; this generalises them): the
+    lid is the top edge (corner 2 to corner 3) and moves along itself at speed
+    U, u_lid = U (x3 - x2, y3 - y2) / |...|; the other walls are at rest, the
+    two top corner nodes too. With the trapezoid's corners this is
+    cavity_grid exactly.
+    """
+    xi = np.linspace(0.0, 1.0, nx)[None, :]
+    eta = np.linspace(0.0, 1.0, ny)[:, None]
+    met = quad_metrics(xi, eta, corners)
+    if np.any(met["J"] <= 0):
+        raise ValueError("corners must make a convex, counter-clockwise quadrilateral")
+    cxi, ceta = contravariant_velocities(met, c)
+    x, y = quad_xy(xi, eta, corners)
+    (x0, y0), (x1, y1), (x2, y2), (x3, y3) = corners
+    tl = math.hypot(x3 - x2, y3 - y2)
+    lid_x, lid_y = np.zeros(nx), np.zeros(nx)
+    lid_x[1:-1] = U * (x3 - x2) / tl
+    lid_y[1:-1] = U * (y3 - y2) / tl
+    z_x, z_y = np.zeros(nx), np.zeros(ny)
+    wall_u = dict(bottom=(z_x, z_x), top=(lid_x, lid_y), left=(z_y, z_y), right=(z_y, z_y))
+    return Grid(nx=nx, ny=ny, dxi=1.0 / (nx - 1), deta=1.0 / (ny - 1), cxi=cxi, ceta=ceta,
+                J=met["J"] + 0.0 * (xi + eta), x_eta=met["x_eta"] + 0.0 * (xi + eta),
+                y_eta=met["y_eta"] + 0.0 * (xi + eta), wall_u=wall_u, x=x + 0.0 * eta,
+                y=y + 0.0 * xi)
+
+
+def quad_run(nx, ny, corners, Re, n, H=1.0, U=0.1, **kw):
+    """Rest-state lid-driven cavity on a general quadrilateral; K from Eq.
+    (2.15.1) with the reference length H."""
+    g = quad_grid(nx, ny, corners, U)
+    prm = cavity_params(nx, ny, Re, n, U=U, H=H, grid=g, **kw)
+    fhat, lam = initial_state(g, prm)
+    return Run(g=g, prm=prm, fhat=fhat, lam=lam)
+
+
 def periodic_grid(nx, ny, Lx=1.0, Ly=1.0, periodic_eta=True, c=1.0):
     """Identity-map test domain (x = Lx xi, y = Ly eta) used by the oracle's pins.
 
