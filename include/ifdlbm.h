@@ -144,6 +144,24 @@ typedef struct {
   double U_lid; /* lid speed U of Eq. (1.5), > 0 */
 } ifdlbm_cavity;
 
+/* One cavity on a general convex quadrilateral (the trapezoid map of
+ * Eq. (3.8.1) generalised to the bilinear map of its corners; the metrics
+ * of Eqs. (3.2)-(3.3) then vary along both grid directions and eta_x need
+ * not vanish). corners = {x0, y0, x1, y1, x2, y2, x3, y3}: bottom-left,
+ * bottom-right, top-left, top-right; xi runs along the bottom edge and the
+ * lid, eta up the side walls. The lid is the top edge and moves along it at
+ * speed U_lid; the other walls and the two top corner nodes are at rest.
+ * H is the reference length of Eq. (2.15.1). */
+typedef struct {
+  int nx;
+  int ny;
+  double corners[8];
+  double H;     /* > 0 */
+  double Re;    /* > 0 */
+  double n;     /* > 0 */
+  double U_lid; /* > 0 */
+} ifdlbm_quad_cavity;
+
 /* Scalar facts about one cavity of a handle. */
 typedef struct {
   int nx, ny;
@@ -193,6 +211,22 @@ int ifdlbm_create(int nx, int ny, ifdlbm_geometry g, double Re, double n, double
  * array of ncav entries; 1 <= ncav <= 4096. */
 int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_options *opt,
                         void *stream, ifdlbm_handle *out);
+
+/* Creates `ncav` cavities on general quadrilaterals (ifdlbm_quad_cavity,
+ * host array). The step keeps one FP64 plane per metric and node (xi_x,
+ * xi_y, eta_x, eta_y, x_eta, y_eta, J: 56 bytes per node) and runs on the
+ * staged kernels: kernel AUTO selects STAGED for both precisions and FUSED
+ * is INVALID_ARG. The default time step applies the Courant number to the
+ * largest contravariant speeds over all nodes (dt_mode CONTRAVARIANT);
+ * dt_mode GRID without an explicit dt is INVALID_ARG. Every other call
+ * takes the handle as it takes a trapezoid handle, except the adjoint
+ * calls (INVALID_ARG). ifdlbm_eddies locates the eddies in (xi, eta) by
+ * the same rule and maps their centres through the corners.
+ * Errors: INVALID_ARG also for non-finite corners, H <= 0, or corners whose
+ * Jacobian is not positive at all four of them (not convex and
+ * counter-clockwise). */
+int ifdlbm_create_quad_batch(int ncav, const ifdlbm_quad_cavity *quads,
+                             const ifdlbm_options *opt, void *stream, ifdlbm_handle *out);
 
 /* Advances every cavity of the handle by `nsteps` >= 0 time steps, Steps
  * (2)-(7) of Sec. 4 (Eqs. 2.8-2.18, 3.6-3.7, non-equilibrium extrapolation

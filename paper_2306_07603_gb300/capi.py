@@ -60,6 +60,12 @@ class ifdlbm_cavity(C.Structure):
                 ("Re", C.c_double), ("n", C.c_double), ("U_lid", C.c_double)]
 
 
+class ifdlbm_quad_cavity(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("corners", C.c_double * 8),
+                ("H", C.c_double), ("Re", C.c_double), ("n", C.c_double),
+                ("U_lid", C.c_double)]
+
+
 class ifdlbm_info_t(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("precision", C.c_int), ("kernel", C.c_int),
                 ("dt", C.c_double), ("K", C.c_double), ("gamma_min", C.c_double),
@@ -94,6 +100,9 @@ _SIGS = {
                                 C.POINTER(_H)]),
     "ifdlbm_create_batch": (C.c_int, [C.c_int, C.POINTER(ifdlbm_cavity),
                                       C.POINTER(ifdlbm_options), C.c_void_p, C.POINTER(_H)]),
+    "ifdlbm_create_quad_batch": (C.c_int, [C.c_int, C.POINTER(ifdlbm_quad_cavity),
+                                           C.POINTER(ifdlbm_options), C.c_void_p,
+                                           C.POINTER(_H)]),
     "ifdlbm_step": (C.c_int, [_H, C.c_int]),
     "ifdlbm_macros": (C.c_int, [_H, _P, _P, _P, _P]),
     "ifdlbm_batch_macros": (C.c_int, [_H, C.c_int, _P, _P, _P, _P]),
@@ -221,6 +230,15 @@ def ifdlbm_create_batch(cavities, opt=None, stream=0):
     _check(load_library().ifdlbm_create_batch(len(cavities), arr,
                                               C.byref(opt) if opt is not None else None,
                                               C.c_void_p(int(stream)), C.byref(h)))
+    return h
+
+
+def ifdlbm_create_quad_batch(quads, opt=None, stream=0):
+    arr = (ifdlbm_quad_cavity * len(quads))(*quads)
+    h = _H()
+    _check(load_library().ifdlbm_create_quad_batch(len(quads), arr,
+                                                   C.byref(opt) if opt is not None else None,
+                                                   C.c_void_p(int(stream)), C.byref(h)))
     return h
 
 

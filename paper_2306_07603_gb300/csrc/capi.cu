@@ -37,6 +37,7 @@ struct ifdlbm_ctx {
   cudaStream_t stream = nullptr;
   ifdlbm_options opt{};
   std::vector<ifdlbm_cavity> spec;
+  std::vector<ifdlbm_quad_cavity> quad;  // general quadrilaterals (empty for trapezoids)
   std::vector<CavDev> cav;
   std::vector<double> courant;
   ifd::Bufs b{};
@@ -379,12 +380,55 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   return IFDLBM_OK;
 }
 
-int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_options *opt_in,
-                        void *stream, ifdlbm_handle *out) {
-  if (!out) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "out is NULL");
-  *out = nullptr;
-  if (ncav < 1 || ncav > 4096 || !cavs)
-    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "ncav must be in [1, 4096] with a cavity array");
+}  // extern "C"
+
+namespace {
+
+// Metrics of the bilinear map of a general quadrilateral at (xi, eta),
+// Eqs. (3.2)-(3.3): m = xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J.
+void quad_node_metrics(const double *cr, double xi, double eta, double m[7]) {
+  const double x0 = cr[0], y0 = cr[1], x1 = cr[2], y1 = cr[3], x2 = cr[4], y2 = cr[5],
+               x3 = cr[6], y3 = cr[7];
+  const double x_xi = (1 - eta) * (x1 - x0) + eta * (x3 - x2);
+  const double y_xi = (1 - eta) * (y1 - y0) + eta * (y3 - y2);
+  const double x_eta = (1 - xi) * (x2 - x0) + xi * (x3 - x1);
+  const double y_eta = (1 - xi) * (y2 - y0) + xi * (y3 - y1);
+  const double J = x_xi * y_eta - x_eta * y_xi;
+  m[0] = y_eta / J;
+  m[1] = -x_eta / J;
+  m[2] = -y_xi / J;
+  m[3] = x_xi / J;
+  m[4] = x_eta;
+  m[5] = y_eta;
+  m[6] = J;
+}
+
+int validate_quad(ifdlbm_ctx *h, int idx, const ifdlbm_quad_cavity &q) {
+  char buf[256];
+  auto bad = [&](const char *what) {
+    std::snprintf(buf, sizeof buf, "quad cavity %d: %s", idx, what);
+    return fail(h, IFDLBM_ERR_INVALID_ARG, buf);
+  };
+  for (double v : q.corners)
+    if (!std::isfinite(v)) return bad("corners must be finite");
+  if (!(q.H > 0) || !std::isfinite(q.H)) return bad("H must be > 0");
+  // J is bilinear in (xi, eta): positive at the four corners means positive everywhere
+  for (double xi : {0.0, 1.0})
+    for (double eta : {0.0, 1.0}) {
+      double m[7];
+      quad_node_metrics(q.corners, xi, eta, m);
+      if (!(m[6] > 0)) return bad("corners must make a convex, counter-clockwise quadrilateral");
+    }
+  const double tl = std::hypot(q.corners[6] - q.corners[4], q.corners[7] - q.corners[5]);
+  if (!(tl > 0)) return bad("the top edge has zero length");
+  return IFDLBM_OK;
+}
+
+// Shared by ifdlbm_create_batch (trapezoids) and ifdlbm_create_quad_batch
+// (general quadrilaterals: `quads` non-NULL; `cavs` then holds their sizes
+// and flow parameters).
+int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *quads,
+                const ifdlbm_options *opt_in, void *stream, ifdlbm_handle *out) {
   ifdlbm_options opt;
   if (opt_in)
     opt = *opt_in;
@@ -411,6 +455,12 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_rows must be 0 or >= 2");
   if (opt.graph_chunk < 0 || (opt.graph_chunk % 2) != 0)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: graph_chunk must be 0 or even and > 0");
+  if (quads && opt.kernel == IFDLBM_KERNEL_FUSED)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
+                "general quadrilaterals run on the staged kernels (kernel AUTO or STAGED)");
+  if (quads && opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_GRID)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
+                "dt_mode GRID is defined for trapezoids; give dt or use CONTRAVARIANT");
 
   auto *h = new ifdlbm_ctx();
   h->alloc = g_alloc;
@@ -418,6 +468,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->alloc_ctx = g_alloc_ctx;
   for (int k = 0; k < ncav; ++k) {
     int rc = validate(h, k, cavs[k]);
+    if (!rc && quads) rc = validate_quad(h, k, quads[k]);
     if (rc) {
       g_create_error = h->err;
       delete h;
@@ -436,12 +487,14 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->precision = opt.precision;
   h->kernel = opt.kernel != IFDLBM_KERNEL_AUTO
                   ? opt.kernel
-                  : (opt.precision == IFDLBM_FP32DEV ? IFDLBM_KERNEL_FUSED : IFDLBM_KERNEL_STAGED);
+                  : (opt.precision == IFDLBM_FP32DEV && !quads ? IFDLBM_KERNEL_FUSED
+                                                               : IFDLBM_KERNEL_STAGED);
   h->fused_nt = opt.fused_threads ? opt.fused_threads : 128;
   const bool fused = h->kernel == IFDLBM_KERNEL_FUSED;
   h->stream = (cudaStream_t)stream;
   if (h->stream == nullptr) h->opt.graph_chunk = 0;  // the legacy stream cannot be captured
   h->spec.assign(cavs, cavs + ncav);
+  if (quads) h->quad.assign(quads, quads + ncav);
 
   const size_t tsize = opt.precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
   int64_t off = 0, goff = 0;
@@ -449,6 +502,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->cav.resize(ncav);
   h->courant.resize(ncav);
   std::vector<double> xix, xeH, xxi, xeta;
+  std::vector<double> gmet_h;  // per-node metric planes of general quadrilaterals
   for (int k = 0; k < ncav; ++k) {
     const ifdlbm_cavity &s = cavs[k];
     CavDev &cv = h->cav[k];
@@ -476,7 +530,39 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
     cv.implicit = opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
-    if (opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_CONTRAVARIANT) {
+    if (quads) gmet_h.resize(7 * size_t(off));
+    cv.general = quads ? 1 : 0;
+    cv.lid_ux = s.U_lid;
+    cv.lid_uy = 0.0;
+    if (quads) {
+      // per-node metric planes; the lid moves along the top edge (corner 2 to 3)
+      const double *cr = quads[k].corners;
+      const double tl = std::hypot(cr[6] - cr[4], cr[7] - cr[5]);
+      cv.lid_ux = s.U_lid * (cr[6] - cr[4]) / tl;
+      cv.lid_uy = s.U_lid * (cr[7] - cr[5]) / tl;
+      for (int j = 0; j < s.ny; ++j)
+        for (int i = 0; i < s.nx; ++i) {
+          double m[7];
+          quad_node_metrics(cr, double(i) / (s.nx - 1), double(j) / (s.ny - 1), m);
+          const int64_t node = int64_t(j) * cv.pitch + i;
+          for (int t = 0; t < 7; ++t) gmet_h[7 * cv.off + t * cv.plane + node] = m[t];
+        }
+    }
+    if (quads && opt.dt <= 0) {
+      // CFL on the contravariant speeds of Eq. (3.4), maxima over all nodes
+      double mxi = 0.0, meta = 0.0;
+      for (int j = 0; j < s.ny; ++j)
+        for (int i = 0; i < s.nx; ++i) {
+          const double *m = &gmet_h[7 * cv.off + int64_t(j) * cv.pitch + i];
+          for (int q = 1; q < 9; ++q) {
+            static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+            static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+            mxi = std::max(mxi, std::fabs(opt.c * (EX[q] * m[0] + EY[q] * m[cv.plane])));
+            meta = std::max(meta, std::fabs(opt.c * (EX[q] * m[2 * cv.plane] + EY[q] * m[3 * cv.plane])));
+          }
+        }
+      cv.dt = opt.cfl * std::min((1.0 / (s.nx - 1)) / mxi, (1.0 / (s.ny - 1)) / meta);
+    } else if (opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_CONTRAVARIANT) {
       // CFL applied to the contravariant speeds of Eq. (3.4): their largest
       // magnitudes sit at the ends of the xi range and at eta = 0 (x_xi smallest)
       double mxi = 0.0;
@@ -527,13 +613,20 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
       xeH[cv.goff + i] = x_eta / H;
     }
     for (int j = 0; j < s.ny; ++j)
-      for (int i = 0; i < s.nx; i += std::max(1, s.nx - 1))
+      for (int i = 0; i < s.nx; i += quads ? 1 : std::max(1, s.nx - 1))
         for (int q = 1; q < 9; ++q) {
           static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
           static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-          const double A = opt.c * xix[cv.goff + j];
-          const double cxi = A * (EX[q] - EY[q] * xeH[cv.goff + i]);
-          const double ceta = opt.c * EY[q] / H;
+          double cxi, ceta;
+          if (quads) {
+            const double *m = &gmet_h[7 * cv.off + int64_t(j) * cv.pitch + i];
+            cxi = opt.c * (EX[q] * m[0] + EY[q] * m[cv.plane]);
+            ceta = opt.c * (EX[q] * m[2 * cv.plane] + EY[q] * m[3 * cv.plane]);
+          } else {
+            const double A = opt.c * xix[cv.goff + j];
+            cxi = A * (EX[q] - EY[q] * xeH[cv.goff + i]);
+            ceta = opt.c * EY[q] / H;
+          }
           cmax = std::max(cmax, cv.dt * (std::fabs(cxi) / cv.dxi + std::fabs(ceta) / cv.deta));
         }
     h->courant[k] = cmax;
@@ -581,6 +674,8 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   ok &= (h->b.pref = (double *)A(size_t(ncav) * sizeof(double))) != nullptr;
   ok &= (h->b.cav_done = (int *)A(size_t(ncav) * sizeof(int))) != nullptr;
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
+  double *gmet = nullptr;
+  if (quads) ok &= (gmet = (double *)A(gmet_h.size() * sizeof(double))) != nullptr;
   if (!ok) {
     release_all(h);
     delete h;
@@ -592,6 +687,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   h->b.geo.xeta = geo + 3 * goff;
   h->b.geo.cxix_f = geof;
   h->b.geo.jac_f = geof + goff;
+  h->b.geo.gmet = gmet;
   std::vector<float> geof_h(2 * goff);
   for (int k = 0; k < ncav; ++k) {
     const CavDev &cv = h->cav[k];
@@ -613,7 +709,7 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   cudaStream_t s = h->stream;
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
                          geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
-                         ifd::POW_TABLE_SIZE * sizeof(double));
+                         ifd::POW_TABLE_SIZE * sizeof(double) + gmet_h.size() * sizeof(double));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -624,6 +720,9 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(geof, geof_h.data(), geof_h.size() * sizeof(float), cudaMemcpyHostToDevice,
                         s);
+  if (gmet && e == cudaSuccess)
+    e = cudaMemcpyAsync(gmet, gmet_h.data(), gmet_h.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
   static std::vector<double> powtab_h = [] {
     std::vector<double> t(ifd::POW_TABLE_SIZE);
     ifd::fill_pow_tables(t.data());
@@ -671,6 +770,39 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
   }
   *out = h;
   return IFDLBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_options *opt,
+                        void *stream, ifdlbm_handle *out) {
+  if (!out) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ncav < 1 || ncav > 4096 || !cavs)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "ncav must be in [1, 4096] with a cavity array");
+  return create_impl(ncav, cavs, nullptr, opt, stream, out);
+}
+
+int ifdlbm_create_quad_batch(int ncav, const ifdlbm_quad_cavity *quads,
+                             const ifdlbm_options *opt, void *stream, ifdlbm_handle *out) {
+  if (!out) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (ncav < 1 || ncav > 4096 || !quads)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "ncav must be in [1, 4096] with a cavity array");
+  // sizes and flow parameters in the trapezoid record; its geometry (unit
+  // square) serves only the shared checks, the metrics come from the corners
+  std::vector<ifdlbm_cavity> cavs(ncav);
+  for (int k = 0; k < ncav; ++k) {
+    cavs[k].nx = quads[k].nx;
+    cavs[k].ny = quads[k].ny;
+    cavs[k].geom = ifdlbm_geometry{1.0, quads[k].H, 90.0};
+    cavs[k].Re = quads[k].Re;
+    cavs[k].n = quads[k].n;
+    cavs[k].U_lid = quads[k].U_lid;
+  }
+  return create_impl(ncav, cavs.data(), quads, opt, stream, out);
 }
 
 int ifdlbm_create(int nx, int ny, ifdlbm_geometry g, double Re, double n, double U_lid,
@@ -779,7 +911,22 @@ int ifdlbm_eddies(ifdlbm_handle h, int cavity, ifdlbm_eddy out[3]) {
   std::vector<double> psi(size_t(s.nx) * s.ny);
   int rc = ifdlbm_batch_macros(h, cavity, nullptr, nullptr, nullptr, psi.data());
   if (rc) return rc;
-  rc = ifdlbm_find_eddies(s.nx, s.ny, s.geom, psi.data(), out);
+  if (h->quad.empty()) {
+    rc = ifdlbm_find_eddies(s.nx, s.ny, s.geom, psi.data(), out);
+  } else {
+    // the finder works in (xi, eta) (unit-square geometry: x = xi, y = eta);
+    // the centres are then mapped through the bilinear map of the corners
+    rc = ifdlbm_find_eddies(s.nx, s.ny, ifdlbm_geometry{1.0, 1.0, 90.0}, psi.data(), out);
+    const double *cr = h->quad[cavity].corners;
+    for (int k = 0; k < 3 && !rc; ++k)
+      if (out[k].found) {
+        const double xi = out[k].xi, eta = out[k].eta;
+        const double w0 = (1 - xi) * (1 - eta), w1 = xi * (1 - eta), w2 = (1 - xi) * eta,
+                     w3 = xi * eta;
+        out[k].x = w0 * cr[0] + w1 * cr[2] + w2 * cr[4] + w3 * cr[6];
+        out[k].y = w0 * cr[1] + w1 * cr[3] + w2 * cr[5] + w3 * cr[7];
+      }
+  }
   if (rc) return fail(h, rc, "eddies: " + std::string(ifdlbm_last_error(nullptr)));
   return IFDLBM_OK;
 }
@@ -965,6 +1112,8 @@ int adjoint_ready(ifdlbm_ctx *h) {
     return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: needs a FP64 handle with the staged kernels");
   if (h->opt.lambda_mode != IFDLBM_LAMBDA_LAGGED)
     return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the lagged relaxation time");
+  if (!h->quad.empty())
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the trapezoid map of Eq. (3.8.1)");
   if (h->adj_g1) return IFDLBM_OK;
   const size_t P = size_t(h->total_plane) * sizeof(double);
   bool ok = true;

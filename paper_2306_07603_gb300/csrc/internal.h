@@ -31,7 +31,8 @@ struct CavDev {
   double lnHU;              // ln H - ln U: d ln K / d n (adjoint)
   double Re;                // Reynolds number (adjoint)
   int implicit;             // 1: lambda from the implicit form of Eq. (2.14), 0: lagged
-  int pad_;
+  int general;              // 1: general quadrilateral, per-node metrics in Geo::gmet
+  double lid_ux, lid_uy;    // lid velocity (U, 0) on the trapezoid, U along the top edge in general
 };
 
 // 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
@@ -44,6 +45,9 @@ struct CavDev {
 struct Geo {
   const double *xix, *xeH, *xxi, *xeta;
   const float *cxix_f, *jac_f;
+  // general quadrilaterals (staged kernels): per node, at 7 * off + k * plane,
+  // k = 0..6: xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J (Eqs. 3.2-3.3)
+  const double *gmet;
 };
 
 // Device buffers of a handle. T is double (FP64) or float (FP32DEV).

@@ -119,11 +119,48 @@ __device__ __forceinline__ T advect(const T *F, int64_t node, int pitch, int i, 
 }
 
 __device__ __forceinline__ void wall_neighbour(const CavDev &cv, int i, int j, int &ii, int &jj,
-                                               bool &wall, double &uwx) {
+                                               bool &wall, double &uwx, double &uwy) {
   wall = (i == 0) | (j == 0) | (i == cv.nx - 1) | (j == cv.ny - 1);
   ii = min(max(i, 1), cv.nx - 2);
   jj = min(max(j, 1), cv.ny - 2);
-  uwx = (j == cv.ny - 1 && i > 0 && i < cv.nx - 1) ? cv.U : 0.0;
+  const bool lid = j == cv.ny - 1 && i > 0 && i < cv.nx - 1;
+  uwx = lid ? cv.lid_ux : 0.0;
+  uwy = lid ? cv.lid_uy : 0.0;
+}
+
+// Contravariant velocities of Eq. (3.4) at a node: from the separable
+// trapezoid metrics (A = c xi_x(eta), B = A x_eta(xi)/H, c_eta = c e_y / H),
+// or from the per-node metric planes of a general quadrilateral.
+struct NodeMetrics {
+  bool general;
+  double A, B, ceta_unit, xix, xiy, etx, ety;
+};
+__device__ __forceinline__ NodeMetrics node_metrics(const CavDev &cv, const Geo &geo, int ii,
+                                                    int jj, int64_t node) {
+  NodeMetrics m;
+  m.general = cv.general != 0;
+  m.A = cv.c * geo.xix[cv.goff + jj];
+  m.B = m.A * geo.xeH[cv.goff + ii];
+  m.ceta_unit = cv.c / cv.H;
+  m.xix = m.xiy = m.etx = m.ety = 0.0;
+  if (m.general) {
+    const double *gm = geo.gmet + 7 * cv.off;
+    m.xix = cv.c * gm[node];
+    m.xiy = cv.c * gm[cv.plane + node];
+    m.etx = cv.c * gm[2 * cv.plane + node];
+    m.ety = cv.c * gm[3 * cv.plane + node];
+  }
+  return m;
+}
+__device__ __forceinline__ void contravariant(const NodeMetrics &m, int q, double &cxi,
+                                              double &ceta) {
+  if (m.general) {
+    cxi = ex(q) * m.xix + ey(q) * m.xiy;
+    ceta = ex(q) * m.etx + ey(q) * m.ety;
+  } else {
+    cxi = cxi_of(q, m.A, m.B);
+    ceta = ey(q) * m.ceta_unit;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -136,25 +173,23 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   const CavDev &cv = a.cav[r.cav];
   int ii, jj;
   bool wall;
-  double uwx;
-  wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx);
+  double uwx, uwy;
+  wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx, uwy);
   const int64_t b9 = 9 * cv.off;
   const T *fb = (const T *)a.fb + b9;
   const int64_t node = int64_t(jj) * cv.pitch + ii;
   const double lam = a.lam_out[cv.off + node];
 
-  const double A = cv.c * a.geo.xix[cv.goff + jj];         // c xi_x
-  const double B = A * a.geo.xeH[cv.goff + ii];            // c xi_x x_eta / H
-  const T ceta_unit = T(cv.c / cv.H);
+  const NodeMetrics met = node_metrics(cv, a.geo, ii, jj, node);
   const T hdt = T(0.5 * cv.dt);
   T fbar[9];
   fbar[0] = fb[node];
 #pragma unroll
   for (int q = 1; q < 9; ++q) {
     const T *F = fb + q * cv.plane;
-    const T cxi = T(cxi_of(q, A, B));
-    const T ceta = T(ey(q)) * ceta_unit;
-    fbar[q] = F[node] - hdt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, cxi, ceta, cv);
+    double cx, ce;
+    contravariant(met, q, cx, ce);
+    fbar[q] = F[node] - hdt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, T(cx), T(ce), cv);
   }
   const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
   T ux, uy, P;
@@ -166,7 +201,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   T fh[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) fh[q] = toward(fbar[q], geq[q], bh);
-  if (wall) nee(fh, T(uwx), T(0), cv);
+  if (wall) nee(fh, T(uwx), T(uwy), cv);
   store9((T *)a.fh + b9, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
 }
 
@@ -181,27 +216,25 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
   if (r.valid) {
     int ii, jj;
     bool wall;
-    double uwx;
-    wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx);
+    double uwx, uwy;
+    wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx, uwy);
     const int64_t b9 = 9 * cv.off;
     const T *fh = (const T *)a.fh + b9;
     const T *fp = (const T *)a.fp + b9;
     const int64_t node = int64_t(jj) * cv.pitch + ii;
-    const double A = cv.c * a.geo.xix[cv.goff + jj];
-    const double B = A * a.geo.xeH[cv.goff + ii];
-    const T ceta_unit = T(cv.c / cv.H);
+    const NodeMetrics met = node_metrics(cv, a.geo, ii, jj, node);
     const T dt = T(cv.dt);
     T gn[9];
     gn[0] = fp[node];
 #pragma unroll
     for (int q = 1; q < 9; ++q) {
       const T *F = fh + q * cv.plane;
-      const T cxi = T(cxi_of(q, A, B));
-      const T ceta = T(ey(q)) * ceta_unit;
+      double cx, ce;
+      contravariant(met, q, cx, ce);
       gn[q] = fp[q * cv.plane + node] -
-              dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, cxi, ceta, cv);  // Eq. (3.6)
+              dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, T(cx), T(ce), cv);  // Eq. (3.6)
     }
-    if (wall) nee(gn, T(uwx), T(0), cv);
+    if (wall) nee(gn, T(uwx), T(uwy), cv);
     const int64_t me = int64_t(r.j) * cv.pitch + r.i;
     store9((T *)a.g_out + b9, cv.plane, me, gn);
 
@@ -221,7 +254,9 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
       p.u2max = p.u2;
       const double wx = ((r.i == 0 || r.i == cv.nx - 1) ? 0.5 : 1.0) * cv.dxi;
       const double wy = ((r.j == 0 || r.j == cv.ny - 1) ? 0.5 : 1.0) * cv.deta;
-      p.ek = 0.5 * wx * wy * (a.geo.xxi[cv.goff + r.j] * cv.H) * p.u2;  // Eq. (5.1)
+      const double J = cv.general ? a.geo.gmet[7 * cv.off + 6 * cv.plane + me]
+                                  : a.geo.xxi[cv.goff + r.j] * cv.H;
+      p.ek = 0.5 * wx * wy * J * p.u2;  // Eq. (5.1)
     }
   }
   if (a.want_residual) block_partial<TILE_X * TILE_Y / 32>(p, a.part, blockIdx.x);
@@ -245,7 +280,8 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_init(const CavDev *cavs, con
   const int64_t node = int64_t(r.j) * cv.pitch + r.i;
   const bool lid = r.j == cv.ny - 1 && r.i > 0 && r.i < cv.nx - 1;
   T geq[9];
-  equilibrium(T(0), lid ? T(cv.U) : T(0), T(0), T(cv.c), T(cv.inv_cs2), geq);
+  equilibrium(T(0), lid ? T(cv.lid_ux) : T(0), lid ? T(cv.lid_uy) : T(0), T(cv.c),
+              T(cv.inv_cs2), geq);
   store9(g + 9 * cv.off, cv.plane, node, geq);
   lam[cv.off + node] = cv.lam0;
 }
@@ -260,7 +296,7 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cv.nx) return;
   const T *gb = g + 9 * cv.off;
-  const double xeta = geo.xeta[cv.goff + i];
+  const double *gm = cv.general ? geo.gmet + 7 * cv.off : nullptr;
   double acc = 0.0, Iprev = 0.0;
   for (int j = 0; j < cv.ny; ++j) {
     T gg[9];
@@ -271,7 +307,9 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *
     if (rho) rho[o] = cv.rho0 + (p0 + double(P)) * cv.inv_cs2;
     if (u) u[o] = double(ux);
     if (v) v[o] = double(uy);
-    const double I = double(ux) * cv.H - double(uy) * xeta;
+    const int64_t nd = int64_t(j) * cv.pitch + i;
+    const double I = cv.general ? double(ux) * gm[5 * cv.plane + nd] - double(uy) * gm[4 * cv.plane + nd]
+                                : double(ux) * cv.H - double(uy) * geo.xeta[cv.goff + i];
     if (j > 0) acc += 0.5 * (I + Iprev) * cv.deta;
     Iprev = I;
     if (psi) psi[o] = acc;

@@ -45,7 +45,21 @@ def cavity(nx, ny, Re, n, theta_deg=60.0, U_lid=0.1, L=1.0, H=1.0):
                               float(Re), float(n), float(U_lid))
 
 
+def quad_cavity(nx, ny, corners, Re, n, U_lid=0.1, H=1.0):
+    """A cavity on a general quadrilateral (ifdlbm_quad_cavity); corners are
+    ((x0, y0) bottom-left, (x1, y1) bottom-right, (x2, y2) top-left,
+    (x3, y3) top-right), the lid being the top edge."""
+    flat = [float(v) for xy in corners for v in xy]
+    if len(flat) != 8:
+        raise ValueError("corners: four (x, y) pairs")
+    return capi.ifdlbm_quad_cavity(int(nx), int(ny), (capi.C.c_double * 8)(*flat), float(H),
+                                   float(Re), float(n), float(U_lid))
+
+
 class Solver:
+    """Owns one handle over a batch of cavities: all ``cavity(...)`` records
+    (trapezoids) or all ``quad_cavity(...)`` records (general quadrilaterals)."""
+
     def __init__(self, cavities, stream=None, **options):
         import torch
 
@@ -56,7 +70,11 @@ class Solver:
         self.stream = stream if stream is not None else torch.cuda.Stream()
         self.cavities = list(cavities)
         self.opt = make_options(**options)
-        self.h = capi.ifdlbm_create_batch(self.cavities, self.opt, self.stream.cuda_stream)
+        quads = [isinstance(c, capi.ifdlbm_quad_cavity) for c in self.cavities]
+        if any(quads) and not all(quads):
+            raise ValueError("a batch holds either trapezoid or quadrilateral cavities")
+        create = capi.ifdlbm_create_quad_batch if any(quads) else capi.ifdlbm_create_batch
+        self.h = create(self.cavities, self.opt, self.stream.cuda_stream)
 
     @property
     def ncav(self):

@@ -92,3 +92,39 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ifdlbm_sync(None) == capi.IFDLBM_ERR_INVALID_ARG
     assert lib.ifdlbm_destroy(None) == capi.IFDLBM_OK
     assert lib.ifdlbm_state_bytes(None) == -1
+
+
+SKEW = ((0.1, -0.05), (1.3, 0.12), (-0.2, 0.9), (1.05, 1.1))
+
+
+@pytest.mark.parametrize("corners,kw,frag", [
+    (((0, 0), (1, 0), (1, 1), (0, 1)), {}, "convex"),          # top corners swapped: J < 0
+    (((0, 0), (1, 0), (0, 1), (0.0, 1.0)), {}, "convex"),      # degenerate: J = 0 at a corner
+    (((0, 0), (1, 0), (0, 1), (float("nan"), 1.0)), {}, "finite"),
+    (SKEW, {"H": 0.0}, "H must"),
+    (SKEW, {"Re": -1.0}, "Re, n"),
+])
+def test_invalid_quadrilaterals_rejected_before_device_use(lib, corners, kw, frag):
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.solver import quad_cavity
+    args = dict(Re=100.0, n=0.75)
+    args.update(kw)
+    q = quad_cavity(9, 9, corners, **args)
+    with pytest.raises(capi.IfdlbmError) as e:
+        capi.ifdlbm_create_quad_batch([q])
+    assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG
+    assert frag in str(e.value)
+
+
+@pytest.mark.parametrize("field,val,frag", [("kernel", 2, "staged kernels"),
+                                            ("dt_mode", 0, "dt_mode GRID")])
+def test_quadrilateral_options_rejected(lib, field, val, frag):
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.solver import quad_cavity
+    assert (capi.IFDLBM_KERNEL_FUSED, capi.IFDLBM_DT_GRID) == (2, 0)
+    o = capi.ifdlbm_default_options()
+    setattr(o, field, val)
+    with pytest.raises(capi.IfdlbmError) as e:
+        capi.ifdlbm_create_quad_batch([quad_cavity(9, 9, SKEW, 100.0, 0.75)], o)
+    assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG
+    assert frag in str(e.value)
