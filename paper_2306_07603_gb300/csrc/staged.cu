@@ -128,45 +128,49 @@ __device__ __forceinline__ void wall_neighbour(const CavDev &cv, int i, int j, i
   uwy = lid ? cv.lid_uy : 0.0;
 }
 
-// Contravariant velocities of Eq. (3.4) at a node: from the separable
-// trapezoid metrics (A = c xi_x(eta), B = A x_eta(xi)/H, c_eta = c e_y / H),
-// or from the per-node metric planes of a general quadrilateral.
+// Contravariant velocities of Eq. (3.4) at a node. GEN = false: the
+// separable trapezoid metrics (A = c xi_x(eta), B = A x_eta(xi)/H,
+// c_eta = c e_y / H); GEN = true: the per-node metric planes of a general
+// quadrilateral (a handle holds one kind only, so the kind is a template
+// parameter and the trapezoid kernels carry no trace of the general one).
+template <bool GEN>
 struct NodeMetrics {
-  bool general;
-  double A, B, ceta_unit, xix, xiy, etx, ety;
+  double a, b, c, d;  // A, B, c/H, - (trapezoid); c xi_x, c xi_y, c eta_x, c eta_y (general)
 };
-__device__ __forceinline__ NodeMetrics node_metrics(const CavDev &cv, const Geo &geo, int ii,
-                                                    int jj, int64_t node) {
-  NodeMetrics m;
-  m.general = cv.general != 0;
-  m.A = cv.c * geo.xix[cv.goff + jj];
-  m.B = m.A * geo.xeH[cv.goff + ii];
-  m.ceta_unit = cv.c / cv.H;
-  m.xix = m.xiy = m.etx = m.ety = 0.0;
-  if (m.general) {
+template <bool GEN>
+__device__ __forceinline__ NodeMetrics<GEN> node_metrics(const CavDev &cv, const Geo &geo, int ii,
+                                                         int jj, int64_t node) {
+  NodeMetrics<GEN> m;
+  if constexpr (GEN) {
     const double *gm = geo.gmet + 7 * cv.off;
-    m.xix = cv.c * gm[node];
-    m.xiy = cv.c * gm[cv.plane + node];
-    m.etx = cv.c * gm[2 * cv.plane + node];
-    m.ety = cv.c * gm[3 * cv.plane + node];
+    m.a = cv.c * gm[node];
+    m.b = cv.c * gm[cv.plane + node];
+    m.c = cv.c * gm[2 * cv.plane + node];
+    m.d = cv.c * gm[3 * cv.plane + node];
+  } else {
+    m.a = cv.c * geo.xix[cv.goff + jj];
+    m.b = m.a * geo.xeH[cv.goff + ii];
+    m.c = cv.c / cv.H;
+    m.d = 0.0;
   }
   return m;
 }
-__device__ __forceinline__ void contravariant(const NodeMetrics &m, int q, double &cxi,
+template <bool GEN>
+__device__ __forceinline__ void contravariant(const NodeMetrics<GEN> &m, int q, double &cxi,
                                               double &ceta) {
-  if (m.general) {
-    cxi = ex(q) * m.xix + ey(q) * m.xiy;
-    ceta = ex(q) * m.etx + ey(q) * m.ety;
+  if constexpr (GEN) {
+    cxi = ex(q) * m.a + ey(q) * m.b;
+    ceta = ex(q) * m.c + ey(q) * m.d;
   } else {
-    cxi = cxi_of(q, m.A, m.B);
-    ceta = ey(q) * m.ceta_unit;
+    cxi = cxi_of(q, m.a, m.b);
+    ceta = ey(q) * m.c;
   }
 }
 
 // ---------------------------------------------------------------------------
 // Step (4): half step and f(t + dt/2)
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, bool GEN>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   const NodeRef r = tile_node(a.tile_cav, a.cav);
   if (!r.valid) return;
@@ -180,7 +184,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   const int64_t node = int64_t(jj) * cv.pitch + ii;
   const double lam = a.lam_out[cv.off + node];
 
-  const NodeMetrics met = node_metrics(cv, a.geo, ii, jj, node);
+  const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
   const T hdt = T(0.5 * cv.dt);
   T fbar[9];
   fbar[0] = fb[node];
@@ -201,14 +205,14 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   T fh[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) fh[q] = toward(fbar[q], geq[q], bh);
-  if (wall) nee(fh, T(uwx), T(uwy), cv);
+  if (wall) nee(fh, T(uwx), GEN ? T(uwy) : T(0), cv);
   store9((T *)a.fh + b9, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
 }
 
 // ---------------------------------------------------------------------------
 // Steps (5)-(6): full step, wall nodes, residual partials
 // ---------------------------------------------------------------------------
-template <class T>
+template <class T, bool GEN>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
   const NodeRef r = tile_node(a.tile_cav, a.cav);
   const CavDev &cv = a.cav[r.cav];
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
     const T *fh = (const T *)a.fh + b9;
     const T *fp = (const T *)a.fp + b9;
     const int64_t node = int64_t(jj) * cv.pitch + ii;
-    const NodeMetrics met = node_metrics(cv, a.geo, ii, jj, node);
+    const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
     const T dt = T(cv.dt);
     T gn[9];
     gn[0] = fp[node];
@@ -234,7 +238,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
       gn[q] = fp[q * cv.plane + node] -
               dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, T(cx), T(ce), cv);  // Eq. (3.6)
     }
-    if (wall) nee(gn, T(uwx), T(uwy), cv);
+    if (wall) nee(gn, T(uwx), GEN ? T(uwy) : T(0), cv);
     const int64_t me = int64_t(r.j) * cv.pitch + r.i;
     store9((T *)a.g_out + b9, cv.plane, me, gn);
 
@@ -254,8 +258,11 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
       p.u2max = p.u2;
       const double wx = ((r.i == 0 || r.i == cv.nx - 1) ? 0.5 : 1.0) * cv.dxi;
       const double wy = ((r.j == 0 || r.j == cv.ny - 1) ? 0.5 : 1.0) * cv.deta;
-      const double J = cv.general ? a.geo.gmet[7 * cv.off + 6 * cv.plane + me]
-                                  : a.geo.xxi[cv.goff + r.j] * cv.H;
+      double J;
+      if constexpr (GEN)
+        J = a.geo.gmet[7 * cv.off + 6 * cv.plane + me];
+      else
+        J = a.geo.xxi[cv.goff + r.j] * cv.H;
       p.ek = 0.5 * wx * wy * J * p.u2;  // Eq. (5.1)
     }
   }
@@ -458,10 +465,16 @@ template <class T> void launch_collide(const StepArgs &a, int ntiles, cudaStream
   k_collide<T><<<ntiles, kTile, 0, s>>>(a);
 }
 template <class T> void launch_half(const StepArgs &a, int ntiles, cudaStream_t s) {
-  k_half<T><<<ntiles, kTile, 0, s>>>(a);
+  if (a.geo.gmet)
+    k_half<T, true><<<ntiles, kTile, 0, s>>>(a);
+  else
+    k_half<T, false><<<ntiles, kTile, 0, s>>>(a);
 }
 template <class T> void launch_full(const StepArgs &a, int ntiles, cudaStream_t s) {
-  k_full<T><<<ntiles, kTile, 0, s>>>(a);
+  if (a.geo.gmet)
+    k_full<T, true><<<ntiles, kTile, 0, s>>>(a);
+  else
+    k_full<T, false><<<ntiles, kTile, 0, s>>>(a);
 }
 void launch_residual_reduce(const CavDev *cav, const double *part, double *resid, int ncav,
                             cudaStream_t s) {
