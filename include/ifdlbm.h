@@ -409,6 +409,12 @@ int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
                         double *ref);
 
+/* Self-test of the FP32 power the FP32-deviation form uses for Eq. (1.4):
+ * for n DEVICE doubles x[k] (finite, > 0 after rounding to float) writes
+ * out[k] = float(x[k])^float(m) as the library evaluates it, widened to
+ * double, on the handle's stream (no sync). */
+int ifdlbm_selftest_pow_f32(ifdlbm_handle h, int n, const double *x, double m, double *out);
+
 /* Number of kernel launches the library has enqueued since the process
  * started (graph replays count every kernel node). */
 int64_t ifdlbm_launch_count(void);

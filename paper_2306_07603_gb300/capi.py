@@ -124,6 +124,7 @@ _SIGS = {
     "ifdlbm_residual_fields_static": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P, _P, _P, _P,
                                                 C.c_void_p]),
     "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
+    "ifdlbm_selftest_pow_f32": (C.c_int, [_H, C.c_int, _P, C.c_double, _P]),
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
@@ -352,6 +353,11 @@ def ifdlbm_adjoint_step(h, state_n, adj, dparams):
 def ifdlbm_selftest_pow(h, x, m, fast, ref):
     return _check(load_library().ifdlbm_selftest_pow(h, int(x.numel()), _ptr(x), float(m),
                                                      _ptr(fast), _ptr(ref)), h)
+
+
+def ifdlbm_selftest_pow_f32(h, x, m, out):
+    return _check(load_library().ifdlbm_selftest_pow_f32(h, int(x.numel()), _ptr(x), float(m),
+                                                         _ptr(out)), h)
 
 
 def ifdlbm_profile(h, enable):

@@ -1297,6 +1297,18 @@ int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, doubl
   return IFDLBM_OK;
 }
 
+int ifdlbm_selftest_pow_f32(ifdlbm_handle h, int n, const double *x, double m, double *out) {
+  if (!h || n < 0 || (n > 0 && (!x || !out)))
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "selftest_pow_f32: bad arguments");
+  if (n == 0) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  ifd::launch_pow_f32_selftest(n, x, m, out, h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "selftest_pow_f32");
+  return IFDLBM_OK;
+}
+
 int ifdlbm_profile(ifdlbm_handle h, int enable) {
   if (!h) return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "handle is NULL");
   cudaSetDevice(h->device);

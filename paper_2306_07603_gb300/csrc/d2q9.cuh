@@ -138,7 +138,9 @@ static __device__ __noinline__ double lambda_implicit(double a, double lam_start
 // clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) evaluated as
 // K max(q, gamma_min^2)^((n-1)/2) (Eq. 1.4), and lam = mu / c_s^2 (Eq. 2.14).
 // Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i). The strain rate is formed
-// in T (the storage precision); the power law is always evaluated in FP64.
+// in T (the storage precision), and so is the power law: FP64 pow_fast for
+// T = double, FP32 pow_f32 for T = float (clamped in FP32 at the largest
+// float not above gamma_min^2). The implicit form is solved in FP64.
 template <class T>
 __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
                                                   const CavDev &cv, const double *powtab) {
@@ -149,9 +151,15 @@ __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double la
   // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
   const T k = T(-2) / ((T(2) * T(lam_prev) + T(cv.dt)) * T(cv.cs2));
   const T Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;
-  double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
-  q = q > cv.gmin2 ? q : cv.gmin2;
-  return cv.Kics2 * pow_fast(q, cv.half_nm1, powtab);
+  if constexpr (sizeof(T) == 4) {
+    const float q = fmaxf(0.5f * (Sxx * Sxx + 2.0f * Sxy * Sxy + Syy * Syy),
+                          __double2float_rd(cv.gmin2));
+    return double(float(cv.Kics2) * pow_f32(q, float(cv.half_nm1)));
+  } else {
+    double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+    q = q > cv.gmin2 ? q : cv.gmin2;
+    return cv.Kics2 * pow_fast(q, cv.half_nm1, powtab);
+  }
 }
 
 // Second moments of the non-equilibrium deviation d_i = g_i - geq_i.

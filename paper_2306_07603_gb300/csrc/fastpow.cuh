@@ -56,4 +56,15 @@ __device__ __forceinline__ double pow_fast(double x, double m, const double *__r
   return __hiloint2double(__double2hiint(res) + ((N >> 8) << 20), __double2loint(res));
 }
 
+// x^m in FP32 for the FP32-deviation form: 2^(m log2 x) with CUDA's log2f
+// and exp2f (1 and 2 ulp by the CUDA math documentation). For normal x > 0
+// its relative error is about ln2 2^-24 (2 |m log2 x| + |m log2 x|) from the
+// roundings of log2 x and of y = m log2 x, plus 2 ulp: within
+// 3e-7 + 1.3e-7 |m log2 x|. The strain rate it is applied to is itself
+// formed in FP32, and lambda enters the step only through the relaxation
+// weights of Eqs. (2.15)-(2.17), which multiply f - f^eq, so this error
+// reaches the populations far below their FP32 rounding. The GB300 FP64 pipe
+// runs at 1/64 of the FP32 rate; this takes the power off it.
+__device__ __forceinline__ float pow_f32(float x, float m) { return exp2f(m * log2f(x)); }
+
 }  // namespace ifd

@@ -254,6 +254,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const double gmin2 = cv.gmin2, half_nm1 = cv.half_nm1, Kics2 = cv.Kics2;
   // largest float not above gamma_min^2 (so that every clamped q is >= it)
   const float gmin2_f = __double2float_rd(gmin2);
+  const float half_nm1_f = float(half_nm1), Kics2_f = float(Kics2);
   const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
   // Step (2) for this thread's row of iteration `it`: moments, f^eq and
   // lambda(t). The row of iteration it + 1 is formed during the full step of
@@ -282,19 +283,18 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
       return o;
     }
-    // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as relaxation_time)
+    // Eqs. (2.12)-(2.14), (1.4): strain rate and power in T (as relaxation_time)
     const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
-    double q;
     if constexpr (sizeof(T) == 4) {
-      // the strain rate is FP32 here: clamp before widening (one FP32 max
-      // instead of an FP64 compare), with the clamp as the float below gamma_min^2
-      q = double(fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f));
+      // clamp at the float below gamma_min^2; FP32 power (pow_f32)
+      const float q = fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f);
+      o.lam = double(Kics2_f * pow_f32(q, half_nm1_f));
     } else {
-      q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+      double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
       q = q > gmin2 ? q : gmin2;
+      o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     }
-    o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     return o;
   };
   auto take = [&](const Collided &o) {

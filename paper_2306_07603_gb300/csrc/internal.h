@@ -151,6 +151,7 @@ void launch_adjoint_step(const AdjArgs &a, int ntiles, int ncav, double *dparams
 
 // Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
 void fill_pow_tables(double *tab);
+void launch_pow_f32_selftest(int n, const double *x, double m, double *out, cudaStream_t s);
 void launch_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
                          double *ref, cudaStream_t s);
 

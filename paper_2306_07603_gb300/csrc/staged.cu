@@ -456,6 +456,16 @@ void launch_pow_selftest(int n, const double *x, double m, const double *tab, do
   k_pow_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, tab, fast, ref);
 }
 
+__global__ void k_pow_f32_selftest(int n, const double *x, double m, double *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = double(pow_f32(float(x[k]), float(m)));
+}
+
+void launch_pow_f32_selftest(int n, const double *x, double m, double *out, cudaStream_t s) {
+  k_pow_f32_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, out);
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------

@@ -53,3 +53,39 @@ def test_pow_fast_newtonian_exponent_is_exactly_one(handle):
     x = 10.0 ** np.linspace(-12, 8, 1001)
     fast, _ = _run(handle, x, 0.0)
     assert np.all(fast == 1.0)
+
+
+@pytest.mark.parametrize("m", [-0.5, -0.375, -0.25, -0.125, 0.125, 0.25, 0.5, 0.73, 1.0])
+def test_pow_f32_relative_error(handle, m):
+    """The FP32 power of the FP32-deviation form: relative error from the
+    exact float(x)^float(m) within 3e-7 + 1.3e-7 |m log2 x| (the roundings of
+    log2 x and of m log2 x, and the ulps of log2f and exp2f)."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    rng = np.random.default_rng(23456)
+    x = 10.0 ** rng.uniform(-12, 8, size=200000)
+    x = np.concatenate([x, 2.0 ** np.arange(-40, 27), 1.0 + np.arange(256) / 256.0])
+    xf = x.astype(np.float32).astype(np.float64)
+    mf = float(np.float32(m))
+    xd = torch.as_tensor(xf, dtype=torch.float64, device="cuda")
+    out = torch.empty_like(xd)
+    capi.ifdlbm_selftest_pow_f32(handle.h, xd, m, out)
+    handle.stream.synchronize()
+    got = out.cpu().numpy()
+    exact = np.power(xf, mf)
+    rel = np.abs(got - exact) / exact
+    bound = 3e-7 + 1.3e-7 * np.abs(mf * np.log2(xf))
+    assert np.all(rel <= bound), (m, (rel / bound).max(), xf[np.argmax(rel / bound)])
+
+
+def test_pow_f32_newtonian_exponent_is_exactly_one(handle):
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    xd = torch.as_tensor((10.0 ** np.linspace(-12, 8, 1001)).astype(np.float32).astype(np.float64),
+                         device="cuda")
+    out = torch.empty_like(xd)
+    capi.ifdlbm_selftest_pow_f32(handle.h, xd, 0.0, out)
+    handle.stream.synchronize()
+    assert np.all(out.cpu().numpy() == 1.0)
