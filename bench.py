@@ -375,14 +375,19 @@ def run_ours(args):
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
 
-    # the FP64 pipe, which bounds the fused step before HBM does (power law of
-    # Eq. 1.4 in FP64 at 1/64 of the FP32 rate): its utilisation from ncu
+    # what bounds the step before HBM does, from the ncu record of the same
+    # kernel sources: the FP64 pipe (1/64 of the FP32 rate on GB300; the FP64
+    # form) and the schedulers' instruction issue (the FP32-deviation form)
     rec = profile_record(dom, args.precision, args.workload) if dom is not None else None
-    fp64 = None
+    fp64 = issue = None
     if rec is not None and "fp64_pipe_pct_elapsed" in rec:
         fp64 = {"bound": "alu", "unit": "fraction of the FP64 pipe's peak issue rate",
                 "frac": round(rec["fp64_pipe_pct_elapsed"] / 100.0, 3),
                 "source": rec["source"] + " (ncu sm__inst_executed_pipe_fp64, elapsed)"}
+    if rec is not None and "issue_active_pct" in rec:
+        issue = {"bound": "issue", "unit": "fraction of cycles the SM schedulers issue",
+                 "frac": round(rec["issue_active_pct"] / 100.0, 3),
+                 "source": rec["source"] + " (ncu smsp__issue_active, active cycles)"}
     layout = fixed or (tuning_options(tuning) if tuning is not None else {})
     e2e = None
     if not args.no_e2e:
@@ -419,6 +424,7 @@ def run_ours(args):
             "hbm_gbs_algorithmic": round(value * 1e6 * (88 if args.precision == "fp32dev" else 160) / 1e9, 1),
             "roofline": roofline,
             "roofline_fp64": fp64,
+            "roofline_issue": issue,
             "kernels_ms_per_launch": {k: round(v[0] / v[1], 5) for k, v in kern.items()},
             "gpu_launches": launches_all,
             "clocks": clocks,
