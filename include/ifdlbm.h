@@ -266,6 +266,16 @@ int ifdlbm_residual(ifdlbm_handle h, double *out);
 /* Residuals of every cavity, HOST out[4 * ncav] in the order above. */
 int ifdlbm_batch_residual(ifdlbm_handle h, double *out);
 
+/* The same read without waiting: enqueues on the handle's stream the copy of
+ * the [ncav][4] residuals into HOST out and, if status is not NULL, of the
+ * divergence word into HOST *status (bit 0 set: some step produced a
+ * non-finite velocity), and returns at once. out and status should be
+ * page-locked (cudaHostAlloc or equivalent) for the copy to be
+ * asynchronous. They are valid once the stream has reached the copy (an
+ * event recorded after this call, or any synchronising call), so a caller
+ * can read step n's residuals while step n + 1 runs. */
+int ifdlbm_batch_residual_async(ifdlbm_handle h, double *out, unsigned *status);
+
 /* State of cavity `cavity` in the paper's variables: fhat[9][ny][nx]
  * (f-hat of Eq. 2.3, full value, not the FP32 deviation) and
  * lambda_prev[ny][nx] (the relaxation time the next step's Eq. (2.18)

@@ -108,6 +108,7 @@ _SIGS = {
     "ifdlbm_batch_macros": (C.c_int, [_H, C.c_int, _P, _P, _P, _P]),
     "ifdlbm_macros_dev": (C.c_int, [_H, C.c_int, _P, _P, _P, _P]),
     "ifdlbm_residual": (C.c_int, [_H, _P]),
+    "ifdlbm_batch_residual_async": (C.c_int, [_H, _P, _P]),
     "ifdlbm_residual_dev": (C.c_int, [_H, _P]),
     "ifdlbm_probe_dev": (C.c_int, [_H, C.c_int, _P, _P]),
     "ifdlbm_batch_residual": (C.c_int, [_H, _P]),
@@ -277,6 +278,14 @@ def ifdlbm_probe_dev(h, probes, out):
 
 def ifdlbm_batch_residual(h, out):
     return _check(load_library().ifdlbm_batch_residual(h, _ptr(out)), h)
+
+
+def ifdlbm_batch_residual_async(h, out, status=None):
+    """out: page-locked float64 tensor [ncav, 4] (or array); status: page-locked
+    int32 tensor of one element, or None. Valid once the stream reaches the copy."""
+    if status is not None and (status.dtype.itemsize != 4 or status.numel() < 1):
+        raise ValueError("status must hold one 32-bit word")
+    return _check(load_library().ifdlbm_batch_residual_async(h, _ptr(out), _ptr(status)), h)
 
 
 def ifdlbm_get_state(h, cavity, fhat=None, lambda_prev=None):

@@ -940,6 +940,17 @@ int ifdlbm_batch_residual(ifdlbm_handle h, double *out) {
   return check_status(h);
 }
 
+int ifdlbm_batch_residual_async(ifdlbm_handle h, double *out, unsigned *status) {
+  if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
+  cudaSetDevice(h->device);
+  cudaError_t e = cudaMemcpyAsync(out, h->b.resid, size_t(h->ncav) * 4 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && status)
+    e = cudaMemcpyAsync(status, h->b.status, sizeof(unsigned), cudaMemcpyDeviceToHost, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "residual_async copy");
+  return IFDLBM_OK;
+}
+
 int ifdlbm_residual_dev(ifdlbm_handle h, double *out) {
   if (!h || !out) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or out");
   cudaSetDevice(h->device);

@@ -235,6 +235,37 @@ def test_divergence_is_reported_not_hidden():
     assert e.value.code == capi.IFDLBM_ERR_DIVERGED
 
 
+def test_async_residual_read_equals_the_synchronous_one():
+    """ifdlbm_batch_residual_async: the residuals and the divergence word land
+    in page-locked host memory once the stream reaches the copy."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    s = solver([cav(33, 29, 400.0, 0.75, 60.0), cav(17, 21, 100.0, 1.5, 75.0)], kernel="fused")
+    res = torch.full((2, 4), np.nan, dtype=torch.float64, pin_memory=True)
+    st = torch.full((1,), 7, dtype=torch.int32, pin_memory=True)
+    s.step(5)
+    capi.ifdlbm_batch_residual_async(s.h, res, st)
+    ev = torch.cuda.Event()
+    ev.record(s.stream)
+    ev.synchronize()
+    assert int(st[0]) == 0
+    assert np.array_equal(res.numpy(), s.residual())
+    # a non-finite state sets bit 0 of the word
+    run = oracle_run(17, 21, 100.0, 1.5, 75.0)
+    f = run.fhat.copy()
+    f[2, 9, 9] = np.nan
+    s.set_state(1, f, run.lam)
+    s.step(1)
+    capi.ifdlbm_batch_residual_async(s.h, res, st)
+    ev.record(s.stream)
+    ev.synchronize()
+    assert int(st[0]) & 1
+    with pytest.raises(capi.IfdlbmError):
+        s.sync()
+    s.close()
+
+
 @pytest.mark.parametrize("schedule", ["grid", "static", "dynamic"])
 def test_fused_schedules_match_oracle_on_uneven_batch(schedule):
     """Persistent schedules (static largest-first, dynamic atomic counter) give
