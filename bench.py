@@ -45,6 +45,9 @@ ALGO_BYTES = {
     ("half", "fp32dev"): 80, ("half", "fp64"): 152,
     ("full", "fp32dev"): 132, ("full", "fp64"): 240,
 }
+# General quadrilaterals: the staged stencil kernels also read the per-node
+# FP64 metrics (xi_x, xi_y, eta_x, eta_y; k_full also J).
+ALGO_BYTES_GENERAL = {"half": 32, "full": 40}
 FALLBACK_HBM_GBS = 6800.0
 
 
@@ -181,13 +184,26 @@ def kernel_source_digest(kernel="fused"):
     return h.hexdigest()[:16]
 
 
+def _record(d, kernel, precision, workload):
+    """The workload's own record, else (trapezoid workloads only) the kernel's."""
+    e = d.get(f"{kernel}:{precision}:{workload}")
+    if e is None and not is_general(workload):
+        e = d[f"{kernel}:{precision}"]
+    return e
+
+
+def is_general(workload):
+    """Workloads of general quadrilaterals (per-node metrics)."""
+    return workload is not None and workload.startswith("quad")
+
+
 def profile_record(kernel, precision, workload=None):
     """The ncu record of this kernel (and workload) if its sources are unchanged."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get(f"{kernel}:{precision}:{workload}") or d[f"{kernel}:{precision}"]
+        e = _record(d, kernel, precision, workload)
         return e if e.get("src_digest") == kernel_source_digest(kernel) else None
     except Exception:
         return None
@@ -200,7 +216,7 @@ def traffic_per_launch(kernel, precision, lu_per_launch, workload=None):
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get(f"{kernel}:{precision}:{workload}") or d[f"{kernel}:{precision}"]
+        e = _record(d, kernel, precision, workload)
         if e.get("src_digest") != kernel_source_digest(kernel):
             return None
         return float(e["bytes_per_lu"]) * lu_per_launch
@@ -211,13 +227,25 @@ def traffic_per_launch(kernel, precision, lu_per_launch, workload=None):
 # ---------------------------------------------------------------------------
 # Oracle CPU baseline (the only use of oracle/ in this file)
 # ---------------------------------------------------------------------------
+def oracle_run_of(O, spec):
+    """The oracle's rest-state run of one workload cavity (trapezoid or quadrilateral)."""
+    if hasattr(spec, "corners"):
+        return O.quad_run(spec.nx, spec.ny, spec.corners, spec.Re, spec.n, H=spec.H, U=spec.U_lid)
+    return O.cavity_run(spec.nx, spec.Re, spec.n, theta_deg=spec.theta_deg, U=spec.U_lid,
+                        L=spec.L, H=spec.H, ny=spec.ny)
+
+
+def spec_label(spec):
+    shape = "quadrilateral" if hasattr(spec, "corners") else f"theta={spec.theta_deg:g}"
+    return f"{shape}, n={spec.n:g}, Re={spec.Re:g}"
+
+
 def oracle_sample_mlups(spec, seconds):
     """Times the FP64 oracle on one cavity of the workload from rest for about
     `seconds` of single-threaded NumPy work. Returns (MLUPS, steps, seconds)."""
     import oracle as O
 
-    run = O.cavity_run(spec.nx, spec.Re, spec.n, theta_deg=spec.theta_deg, U=spec.U_lid,
-                       L=spec.L, H=spec.H, ny=spec.ny)
+    run = oracle_run_of(O, spec)
     t0 = time.perf_counter()
     run.advance(2)
     per = (time.perf_counter() - t0) / 2
@@ -233,7 +261,7 @@ def cpu_baseline(specs, seconds):
     mlups, n, dt, _ = oracle_sample_mlups(spec, seconds)
     return {"value": round(mlups, 4), "unit": "MLUPS", "cores": 1, "kind": "oracle",
             "sample": f"FP64 NumPy oracle, one {spec.nx}x{spec.ny} cavity of the workload "
-                      f"(theta={spec.theta_deg:g}, n={spec.n:g}, Re={spec.Re:g}) from rest, "
+                      f"({spec_label(spec)}) from rest, "
                       f"{n} steps in {dt:.1f} s, single thread"}
 
 
@@ -244,7 +272,10 @@ def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
     from paper_2306_07603_gb300.solver import Solver, cavity
     from paper_2306_07603_gb300.workloads import WORKLOAD_OPTIONS
 
-    cavs = [cavity(s.nx, s.ny, s.Re, s.n, theta_deg=s.theta_deg, U_lid=s.U_lid, L=s.L, H=s.H)
+    from paper_2306_07603_gb300.solver import quad_cavity
+    cavs = [quad_cavity(s.nx, s.ny, s.corners, s.Re, s.n, U_lid=s.U_lid, H=s.H)
+            if hasattr(s, "corners") else
+            cavity(s.nx, s.ny, s.Re, s.n, theta_deg=s.theta_deg, U_lid=s.U_lid, L=s.L, H=s.H)
             for s in specs]
     opts = dict(WORKLOAD_OPTIONS.get(workload, {}), **extra)
     return Solver(cavs, stream=stream, precision=precision, kernel=kernel, **opts)
@@ -359,6 +390,7 @@ def run_ours(args):
     max_ms, launches_all = reduce_over_ranks(total_ms, launches, world, "cuda")
     value = lu_step * world * args.steps / (max_ms * 1e-3) / 1e6
 
+    general = is_general(args.workload)
     # roofline of the dominant kernel, from its live event times
     peak, peak_src = load_peaks()
     dom = max(kern, key=lambda k: kern[k][0]) if kern else None
@@ -366,7 +398,8 @@ def run_ours(args):
     if dom is not None and (dom, args.precision) in ALGO_BYTES:
         ms, n = kern[dom]
         per_launch_s = ms / n * 1e-3
-        algo = ALGO_BYTES[(dom, args.precision)] * lu_step
+        algo = (ALGO_BYTES[(dom, args.precision)] +
+                (ALGO_BYTES_GENERAL.get(dom, 0) if general else 0)) * lu_step
         achieved = algo / per_launch_s / 1e9
         roofline = {"bound": "hbm", "kernel": DEVICE_KERNEL[dom], "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -560,8 +593,7 @@ def run_reference(args):
     specs = WORKLOADS[args.workload]()
     # one reference step = one time step of one cavity of the workload (a
     # bounded sample), cycling through the cavities
-    runs = [O.cavity_run(sp.nx, sp.Re, sp.n, theta_deg=sp.theta_deg, U=sp.U_lid, L=sp.L, H=sp.H,
-                         ny=sp.ny) for sp in specs]
+    runs = [oracle_run_of(O, sp) for sp in specs]
     for k in range(args.warmup):
         runs[k % len(runs)].advance(1)
     lu = 0

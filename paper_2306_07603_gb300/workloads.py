@@ -16,6 +16,10 @@ draws of the batched sweep are plain NumPy generator calls.
              drawn with numpy.random.default_rng(230607603) in that order
 * adjoint257 257 x 257, theta = 60 deg, n = 0.75, Re = 400
 * roof2049 / roof4097  one large cavity for HBM-roofline measurements
+* quad257    10 cavities of 257 x 257 on general quadrilaterals (per-node
+             metrics): the unit square's corners moved by U[-0.2, 0.2] in x and
+             y, drawn with numpy.random.default_rng(230607604), n and Re as in
+             sweep257
 """
 from __future__ import annotations
 
@@ -33,6 +37,23 @@ class CavitySpec:
     theta_deg: float = 60.0
     U_lid: float = 0.1
     L: float = 1.0
+    H: float = 1.0
+
+    @property
+    def nodes(self) -> int:
+        return self.nx * self.ny
+
+
+@dataclass(frozen=True)
+class QuadSpec:
+    """A cavity on a general quadrilateral: corners ((x, y) bottom-left,
+    bottom-right, top-left, top-right); the lid is the top edge."""
+    nx: int
+    ny: int
+    corners: tuple
+    Re: float
+    n: float
+    U_lid: float = 0.1
     H: float = 1.0
 
     @property
@@ -67,6 +88,18 @@ def adjoint257():
     return [CavitySpec(257, 257, 400.0, 0.75, 60.0)]
 
 
+def quad257(seed=230607604):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in (0.5, 0.75, 1.0, 1.25, 1.5):
+        for Re in (100.0, 1000.0):
+            d = rng.uniform(-0.2, 0.2, size=(4, 2))
+            c = tuple((float(x0 + d[k, 0]), float(y0 + d[k, 1]))
+                      for k, (x0, y0) in enumerate(((0, 0), (1, 0), (0, 1), (1, 1))))
+            out.append(QuadSpec(257, 257, c, Re, n))
+    return out
+
+
 def roof(N):
     return [CavitySpec(N, N, 1000.0, 0.75, 60.0)]
 
@@ -83,6 +116,7 @@ WORKLOADS = {
     "adjoint257": adjoint257,
     "roof2049": lambda: roof(2049),
     "roof4097": lambda: roof(4097),
+    "quad257": quad257,
 }
 
 

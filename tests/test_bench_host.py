@@ -69,3 +69,13 @@ def test_kernel_digest_changes_with_source(tmp_path):
     d1 = bench.kernel_source_digest("fused")
     assert len(d1) == 16 and d1 == bench.kernel_source_digest("fused")
     assert d1 != bench.kernel_source_digest("collide")
+
+
+def test_quad_workload_cavities_are_convex_and_seeded():
+    import oracle as O
+    from paper_2306_07603_gb300.workloads import quad257
+    a, b = quad257(), quad257()
+    assert a == b and len(a) == 10
+    for sp in a:
+        g = O.quad_grid(9, 9, sp.corners)      # raises unless J > 0 everywhere
+        assert g.J.min() > 0.3
