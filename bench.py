@@ -59,6 +59,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="sweep257")
     p.add_argument("--precision", default="fp32dev", choices=["fp32dev", "fp64"])
     p.add_argument("--kernel", default="auto", choices=["auto", "staged", "fused"])
+    p.add_argument("--lambda-mode", default="lagged", choices=["lagged", "implicit"],
+                   help="relaxation time of Eq. (2.14): lagged (the paper's) or implicit")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -268,6 +270,9 @@ def cpu_baseline(specs, seconds):
 # ---------------------------------------------------------------------------
 # The GPU arm
 # ---------------------------------------------------------------------------
+LAMBDA_MODE = "lagged"  # set from --lambda-mode
+
+
 def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
     from paper_2306_07603_gb300.solver import Solver, cavity
     from paper_2306_07603_gb300.workloads import WORKLOAD_OPTIONS
@@ -278,6 +283,8 @@ def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
             cavity(s.nx, s.ny, s.Re, s.n, theta_deg=s.theta_deg, U_lid=s.U_lid, L=s.L, H=s.H)
             for s in specs]
     opts = dict(WORKLOAD_OPTIONS.get(workload, {}), **extra)
+    if LAMBDA_MODE != "lagged":
+        opts["lambda_mode"] = LAMBDA_MODE
     return Solver(cavs, stream=stream, precision=precision, kernel=kernel, **opts)
 
 
@@ -403,7 +410,8 @@ def run_ours(args):
         achieved = algo / per_launch_s / 1e9
         roofline = {"bound": "hbm", "kernel": DEVICE_KERNEL[dom], "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                    "traffic": traffic_per_launch(dom, args.precision, lu_step, args.workload),
+                    "traffic": traffic_per_launch(dom, args.precision, lu_step, args.workload)
+                    if args.lambda_mode == "lagged" else None,
                     "algorithmic_bytes": algo, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
@@ -411,7 +419,9 @@ def run_ours(args):
     # what bounds the step before HBM does, from the ncu record of the same
     # kernel sources: the FP64 pipe (1/64 of the FP32 rate on GB300; the FP64
     # form) and the schedulers' instruction issue (the FP32-deviation form)
-    rec = profile_record(dom, args.precision, args.workload) if dom is not None else None
+    # (the ncu records are of the lagged kernels)
+    rec = (profile_record(dom, args.precision, args.workload)
+           if dom is not None and args.lambda_mode == "lagged" else None)
     fp64 = issue = None
     if rec is not None and "fp64_pipe_pct_elapsed" in rec:
         fp64 = {"bound": "alu", "unit": "fraction of the FP64 pipe's peak issue rate",
@@ -451,7 +461,8 @@ def run_ours(args):
             "config": {"workload": args.workload, "cavities": len(specs),
                        "grids": sorted({f"{sp.nx}x{sp.ny}" for sp in specs}),
                        "lattice_updates_per_step": lu_step, "precision": args.precision,
-                       "kernel": args.kernel, "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                       "kernel": args.kernel, "lambda_mode": args.lambda_mode,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "baseline_metric": BASELINE_METRIC},
             "hbm_gbs_algorithmic": round(value * 1e6 * (88 if args.precision == "fp32dev" else 160) / 1e9, 1),
@@ -620,7 +631,9 @@ def run_reference(args):
 
 
 def main(argv=None):
+    global LAMBDA_MODE
     args = parse_args(argv)
+    LAMBDA_MODE = args.lambda_mode
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

@@ -133,6 +133,43 @@ static __device__ __noinline__ double lambda_implicit(double a, double lam_start
   return lam;
 }
 
+// The same solve in FP32 for the FP32-deviation form, with the FP32 power
+// (pow_f32, relative error ~1e-6 for these arguments): F is then known to
+// about 1e-6 of lam, so the iteration stops once the Newton step is below
+// 4e-6 of lam, after at most 10 iterations. As with the power, this error
+// reaches the populations only through the relaxation weights, far below the
+// FP32 rounding of the stored deviations.
+static __device__ __noinline__ float lambda_implicit_f32(float a, float lam_start,
+                                                         const CavDev &cv) {
+  const float C = float(cv.Kics2), dt = float(cv.dt), m = float(cv.nm1), hm = float(cv.half_nm1);
+  const float lamc = float(cv.lam0);
+  if (cv.nm1 == 0.0) return C;
+  if (a <= float(cv.gmin) * (2.0f * lamc + dt)) return lamc;
+  float lo, hi;
+  if (m < 0.0f) {
+    lo = 0.0f;
+    hi = lamc;
+  } else {
+    lo = lamc;
+    hi = C * pow_f32((a / dt) * (a / dt), hm);
+  }
+  float lam = (lam_start > lo && lam_start < hi) ? lam_start : 0.5f * (lo + hi);
+  for (int it = 0; it < 10; ++it) {
+    const float x = 2.0f * lam + dt;
+    const float g = a / x;
+    const float P = C * pow_f32(g * g, hm);
+    const float F = lam - P;
+    if (F == 0.0f) break;
+    if (F > 0.0f) hi = lam; else lo = lam;
+    float next = lam - F / (1.0f + 2.0f * m * P / x);
+    if (!(next >= lo && next <= hi)) next = 0.5f * (lo + hi);
+    const bool done = fabsf(next - lam) <= 4e-6f * next;
+    lam = next;
+    if (done) break;
+  }
+  return lam;
+}
+
 // Relaxation time of Step (2): strain rate from f^ne (Eqs. 2.12-2.13, with
 // f = f(f-hat, lam_prev) of Eq. 2.18), q = |gamma-dot|^2 = 2 D:D, the
 // clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) evaluated as
@@ -140,13 +177,16 @@ static __device__ __noinline__ double lambda_implicit(double a, double lam_start
 // Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i). The strain rate is formed
 // in T (the storage precision), and so is the power law: FP64 pow_fast for
 // T = double, FP32 pow_f32 for T = float (clamped in FP32 at the largest
-// float not above gamma_min^2). The implicit form is solved in FP64.
+// float not above gamma_min^2), and the implicit form's solve.
 template <class T>
 __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
                                                   const CavDev &cv, const double *powtab) {
   if (cv.implicit) {
     const T G2 = T(0.5) * (Pxx * Pxx + T(2) * Pxy * Pxy + Pyy * Pyy);
-    return lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, powtab);
+    if constexpr (sizeof(T) == 4)
+      return double(lambda_implicit_f32(2.0f * sqrtf(G2) * float(cv.inv_cs2), float(lam_prev), cv));
+    else
+      return lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, powtab);
   }
   // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
   const T k = T(-2) / ((T(2) * T(lam_prev) + T(cv.dt)) * T(cv.cs2));

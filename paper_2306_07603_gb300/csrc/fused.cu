@@ -280,7 +280,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     second_moments(d, c_, pxx, pxy, pyy);
     if constexpr (IMPL) {                                  // implicit form of Eq. (2.14)
       const T G2 = T(0.5) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy);
-      o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
+      if constexpr (sizeof(T) == 4)
+        o.lam = double(lambda_implicit_f32(T(2) * sqrtf(G2) * ics2, float(lam_prev), cv));
+      else
+        o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
       return o;
     }
     // Eqs. (2.12)-(2.14), (1.4): strain rate and power in T (as relaxation_time)

@@ -437,13 +437,18 @@ def test_implicit_lambda_one_step_fp64_parity(nx, ny, Re, n, th, k0, kname):
     compare_state(fg, lg, fo, lo, lam_tol=lam_tol)
 
 
-def test_implicit_lambda_fp32_one_step_error():
-    run = oracle_run(67, 45, 100.0, 0.75, 60.0)
+@pytest.mark.parametrize("kname", ["staged", "fused64x8", "fused128"])
+@pytest.mark.parametrize("nx,ny,Re,n,th", [(67, 45, 100.0, 0.75, 60.0), (41, 37, 400.0, 1.5, 75.0)])
+def test_implicit_lambda_fp32_one_step_error(nx, ny, Re, n, th, kname):
+    """FP32 form: the implicit relaxation time solved in FP32 (Newton on the
+    FP32 power), one step within the FP32 bars of the FP64 oracle."""
+    run = oracle_run(nx, ny, Re, n, th)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
-    prm = O.cavity_params(67, 45, 100.0, 0.75, grid=run.g, implicit_lambda=True)
+    prm = O.cavity_params(nx, ny, Re, n, grid=run.g, implicit_lambda=True)
     fo, lo = O.step(f0, l0, run.g, prm)
-    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev", lambda_mode="implicit")
+    s = solver([cav(nx, ny, Re, n, th)], precision="fp32dev", lambda_mode="implicit",
+               **KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)
