@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -176,13 +177,21 @@ KERNEL_SOURCES = {
 }
 
 
+def _code_only(text):
+    """C/C++ source without comments and with whitespace runs collapsed, so that
+    a comment edit does not retire the ncu record of unchanged code."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_digest(kernel="fused"):
-    """Digest of the device sources a kernel is compiled from."""
+    """Digest of the device code (comments and layout aside) a kernel is compiled from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2306_07603_gb300", "csrc")
     for name in KERNEL_SOURCES.get(kernel, sorted(os.listdir(csrc))):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + b"\0" + f.read())
+        with open(os.path.join(csrc, name), encoding="utf-8") as f:
+            h.update(name.encode() + b"\0" + _code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 
