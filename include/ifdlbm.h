@@ -413,9 +413,10 @@ int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double 
 int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes, void *adj,
                             double *dparams);
 
-/* Self-test of the FP64 power used for Eq. (1.4): for n DEVICE doubles x
- * (finite, > 0) writes fast[k] = the library's table-driven x^m and
- * ref[k] = CUDA's pow(x[k], m), on the handle's stream (no sync). */
+/* Self-test of the FP64 power the FP64 form uses for Eq. (1.4): for n
+ * DEVICE doubles x (finite, > 0) writes fast[k] = the library's
+ * table-driven x^m and ref[k] = CUDA's pow(x[k], m), on the handle's stream
+ * (no sync). */
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
                         double *ref);
 

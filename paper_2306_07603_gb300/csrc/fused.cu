@@ -6,7 +6,7 @@
 // h = 0 takes the even rows of the march, half h = 1 the odd ones. Iteration
 // k (k = j0 - 4, j0 - 2, ...) runs, in half h,
 //
-//   stage A  row k + h     moments, f^eq, lagged power-law lambda (FP64 power),
+//   stage A  row k + h     moments, f^eq, lagged power-law lambda (power in T),
 //                          f-hat^+ (Eq. 2.15), f-bar^+ (Eq. 2.16)
 //   stage 1  row k - 2 + h half step f-bar(t+dt/2) (Eq. 3.7), its moments,
 //                          f(t+dt/2) (Eq. 2.17); wall values by extrapolation
@@ -29,8 +29,9 @@
 // full-step values of columns 1 and nx-2, which the wall columns extrapolate
 // from, are published through a small shared array.
 //
-// FP64 work per node is kept to the power of Eq. (1.4) and the residual
-// accumulation: GB300 issues FP64 at 1/64 of the FP32 rate.
+// GB300 issues FP64 at 1/64 of the FP32 rate. With T = float the power of
+// Eq. (1.4) is FP32 too (pow_f32), and the FP64 work per node is the
+// conversion of lambda, whose plane is FP64, and the residual accumulation.
 #include <cstdint>
 
 #include "d2q9.cuh"
@@ -258,7 +259,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
   // Step (2) for this thread's row of iteration `it`: moments, f^eq and
   // lambda(t). The row of iteration it + 1 is formed during the full step of
-  // iteration it, so that the FP64 power overlaps FP32 work.
+  // iteration it, so that the power overlaps the stencil work.
   T nux = 0, nuy = 0, nP = 0, ngeq[9];
   double nlam = 0.0;
   struct Collided {
