@@ -4,7 +4,9 @@
  * The library advances the incompressible finite-difference lattice
  * Boltzmann method (IFDLBM) of Chen, Chai, Zhao and Shi (arXiv 2306.07603)
  * for a power-law fluid in a lid-driven isosceles trapezoidal cavity that
- * is mapped to a uniform (xi, eta) computational grid (Sec. 4, Eq. 3.8).
+ * is mapped to a uniform (xi, eta) computational grid (Sec. 4, Eq. 3.8),
+ * and in cavities on general convex quadrilaterals (bilinear map,
+ * ifdlbm_create_quad_batch).
  * One call of ifdlbm_step performs Steps (2)-(7) of the paper's calculation
  * process per time step, with Step (8)'s global relative error (Eq. 2.19)
  * formed on the last step of the call.
@@ -53,9 +55,11 @@ extern "C" {
                             equilibrium at a reference pressure (Eq. 2.8 at
                             u = 0), P_ref re-based on the cavity's mean
                             pressure every 1024 steps (a uniform pressure
-                            offset is a neutral, drifting mode); metrics, the
-                            power-law relaxation time and all reductions in
-                            FP64. Every output includes P_ref. */
+                            offset is a neutral, drifting mode). The strain
+                            rate and the power law of Eq. (1.4) are FP32 too
+                            (relative error of lambda ~1e-6); metrics, the
+                            lambda plane and all reductions are FP64. Every
+                            output includes P_ref. */
 
 /* Step kernel organisation. */
 #define IFDLBM_KERNEL_AUTO 0   /* FUSED for FP32DEV, STAGED for FP64 */
@@ -108,9 +112,10 @@ typedef struct {
  * The implicit form solves lambda = K max(gamma-dot(lambda), gamma_min)^(n-1)
  * / c_s^2 at every node, gamma-dot(lambda) = a / (2 lambda + dt) with a from
  * sum_i c_i c_i (f-hat_i - f^eq_i) (Eq. 2.18 at the same lambda), by a
- * bracketed Newton iteration in FP64 (the root is unique: the residual
- * increases strictly with lambda). Both forms share steady states. The
- * adjoint needs the lagged form. */
+ * bracketed Newton iteration (the root is unique: the residual increases
+ * strictly with lambda), in FP64 for IFDLBM_FP64 and in FP32 for
+ * IFDLBM_FP32DEV. Both forms share steady states. The adjoint needs the
+ * lagged form. */
 #define IFDLBM_LAMBDA_LAGGED 0   /* default */
 #define IFDLBM_LAMBDA_IMPLICIT 1
 
