@@ -193,6 +193,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.pref = h->b.pref;
     f.cav_done = h->b.cav_done;
     f.implicit = h->opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
+    f.general = h->quad.empty() ? 0 : 1;
     f.resid = h->b.resid;
     f.want_residual = want_residual ? 1 : 0;
     if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
@@ -455,9 +456,12 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: fused_rows must be 0 or >= 2");
   if (opt.graph_chunk < 0 || (opt.graph_chunk % 2) != 0)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: graph_chunk must be 0 or even and > 0");
-  if (quads && opt.kernel == IFDLBM_KERNEL_FUSED)
+  // general quadrilaterals: the fused kernel has an FP32, lagged-lambda variant
+  const bool quad_fused_ok = opt.precision == IFDLBM_FP32DEV && opt.lambda_mode == IFDLBM_LAMBDA_LAGGED;
+  if (quads && opt.kernel == IFDLBM_KERNEL_FUSED && !quad_fused_ok)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
-                "general quadrilaterals run on the staged kernels (kernel AUTO or STAGED)");
+                "general quadrilaterals: the fused kernel needs FP32DEV and the lagged lambda "
+                "(kernel AUTO or STAGED otherwise)");
   if (quads && opt.dt <= 0 && opt.dt_mode == IFDLBM_DT_GRID)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
                 "dt_mode GRID is defined for trapezoids; give dt or use CONTRAVARIANT");
@@ -487,8 +491,9 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->precision = opt.precision;
   h->kernel = opt.kernel != IFDLBM_KERNEL_AUTO
                   ? opt.kernel
-                  : (opt.precision == IFDLBM_FP32DEV && !quads ? IFDLBM_KERNEL_FUSED
-                                                               : IFDLBM_KERNEL_STAGED);
+                  : (opt.precision == IFDLBM_FP32DEV && (!quads || quad_fused_ok)
+                         ? IFDLBM_KERNEL_FUSED
+                         : IFDLBM_KERNEL_STAGED);
   h->fused_nt = opt.fused_threads ? opt.fused_threads : 128;
   const bool fused = h->kernel == IFDLBM_KERNEL_FUSED;
   h->stream = (cudaStream_t)stream;
@@ -675,7 +680,9 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   ok &= (h->b.cav_done = (int *)A(size_t(ncav) * sizeof(int))) != nullptr;
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
   double *gmet = nullptr;
+  float *qsep = nullptr;  // x_xi, y_xi, x_eta, y_eta of the bilinear maps (fused FP32 kernel)
   if (quads) ok &= (gmet = (double *)A(gmet_h.size() * sizeof(double))) != nullptr;
+  if (quads) ok &= (qsep = (float *)A(size_t(4 * goff) * sizeof(float))) != nullptr;
   if (!ok) {
     release_all(h);
     delete h;
@@ -688,7 +695,25 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->b.geo.cxix_f = geof;
   h->b.geo.jac_f = geof + goff;
   h->b.geo.gmet = gmet;
-  std::vector<float> geof_h(2 * goff);
+  h->b.geo.qxxi_f = qsep;
+  h->b.geo.qyxi_f = qsep ? qsep + goff : nullptr;
+  h->b.geo.qxeta_f = qsep ? qsep + 2 * goff : nullptr;
+  h->b.geo.qyeta_f = qsep ? qsep + 3 * goff : nullptr;
+  std::vector<float> qsep_h(quads ? 4 * goff : 0);
+  for (int k = 0; quads && k < ncav; ++k) {
+    const CavDev &cv = h->cav[k];
+    const double *cr = quads[k].corners;
+    for (int j = 0; j < cv.ny; ++j) {
+      const double eta = double(j) / (cv.ny - 1);
+      qsep_h[cv.goff + j] = float((1 - eta) * (cr[2] - cr[0]) + eta * (cr[6] - cr[4]));
+      qsep_h[goff + cv.goff + j] = float((1 - eta) * (cr[3] - cr[1]) + eta * (cr[7] - cr[5]));
+    }
+    for (int i = 0; i < cv.nx; ++i) {
+      const double xi = double(i) / (cv.nx - 1);
+      qsep_h[2 * goff + cv.goff + i] = float((1 - xi) * (cr[4] - cr[0]) + xi * (cr[6] - cr[2]));
+      qsep_h[3 * goff + cv.goff + i] = float((1 - xi) * (cr[5] - cr[1]) + xi * (cr[7] - cr[3]));
+    }
+  }  std::vector<float> geof_h(2 * goff);
   for (int k = 0; k < ncav; ++k) {
     const CavDev &cv = h->cav[k];
     for (int j = 0; j < cv.ny; ++j) {
@@ -709,7 +734,8 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   cudaStream_t s = h->stream;
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
                          geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
-                         ifd::POW_TABLE_SIZE * sizeof(double) + gmet_h.size() * sizeof(double));
+                         ifd::POW_TABLE_SIZE * sizeof(double) + gmet_h.size() * sizeof(double) +
+                         qsep_h.size() * sizeof(float));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -722,6 +748,9 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
                         s);
   if (gmet && e == cudaSuccess)
     e = cudaMemcpyAsync(gmet, gmet_h.data(), gmet_h.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
+  if (qsep && e == cudaSuccess)
+    e = cudaMemcpyAsync(qsep, qsep_h.data(), qsep_h.size() * sizeof(float),
                         cudaMemcpyHostToDevice, s);
   static std::vector<double> powtab_h = [] {
     std::vector<double> t(ifd::POW_TABLE_SIZE);

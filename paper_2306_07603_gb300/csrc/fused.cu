@@ -132,6 +132,39 @@ struct AdvectAll {
   }
 };
 
+// General quadrilateral (per-node metrics, Eq. 3.4 in full): c_{q xi} =
+// e_qx k_xx + e_qy k_xy and c_{q eta} = e_qx k_ex + e_qy k_ey with
+// (k_xx, k_xy, k_ex, k_ey) = c (xi_x, xi_y, eta_x, eta_y) of the node; both
+// upwind sides are chosen by sign at run time.
+template <int Q, class T>
+__device__ __forceinline__ T advect_q_gen(const T *row, int l, const T col[5], T kxx, T kxy, T kex,
+                                          T key, bool clo, bool chi, bool lo, bool hi, T eta_b,
+                                          T i2dxi, T i2deta) {
+  const T cxi = T(ex(Q)) * kxx + T(ey(Q)) * kxy;
+  const T ceta = T(ex(Q)) * kex + T(ey(Q)) * key;
+  const T f0 = col[2];
+  T adv = cxi * dmix2_sel(row[l - 2], row[l - 1], f0, row[l + 1], row[l + 2], cxi >= T(0), clo,
+                          chi, eta_b) * i2dxi;
+  adv += ceta * dmix2_sel(col[0], col[1], f0, col[3], col[4], ceta >= T(0), lo, hi, eta_b) * i2deta;
+  return adv;
+}
+
+template <class T, int Q, int RS, int BS>
+struct AdvectAllGen {
+  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int l, T kxx,
+                                             T kxy, T kex, T key, bool clo, bool chi, bool lo,
+                                             bool hi, T eta_b, T i2dxi, T i2deta, T scale,
+                                             const T *base, T out[9]) {
+    const T col[5] = {cols[0][Q * RS], cols[1][Q * RS], cols[2][Q * RS], cols[3][Q * RS],
+                      cols[4][Q * RS]};
+    out[Q] = base[Q * BS] - scale * advect_q_gen<Q>(rows + Q * RS, l, col, kxx, kxy, kex, key,
+                                                    clo, chi, lo, hi, eta_b, i2dxi, i2deta);
+    if constexpr (Q < 8)
+      AdvectAllGen<T, Q + 1, RS, BS>::run(rows, cols, l, kxx, kxy, kex, key, clo, chi, lo, hi,
+                                          eta_b, i2dxi, i2deta, scale, base, out);
+  }
+};
+
 // Residual terms of one node, summed over up to LEAF rows in T before they
 // are added to the FP64 partials (a leaf sum; every sum beyond it is FP64).
 template <class T>
@@ -173,7 +206,7 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 
 }  // namespace
 
-template <class T, int NT, bool IMPL>
+template <class T, int NT, bool IMPL, bool GEN>
 __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
   constexpr int NC = NT / 2;
   const Task task = a.tasks[ti];
@@ -185,7 +218,8 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const int nx = cv.nx, ny = cv.ny, pitch = cv.pitch;
   const int64_t plane = cv.plane, goff = cv.goff;
   const double cvc = cv.c, cvH = cv.H;
-  const T Uw = T(cv.U);
+  const T Uw = GEN ? T(cv.lid_ux) : T(cv.U);        // lid velocity
+  const T Uwy = GEN ? T(cv.lid_uy) : T(0);
   const int part0 = cv.part0, nparts = cv.nparts;
   // c xi_x of row j and the Jacobian x_xi H: FP64 metrics for FP64
   // arithmetic, their rounded float copies for FP32 arithmetic.
@@ -224,7 +258,13 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T eta_b = T(cv.eta_b);
   const T i2dxi = T(cv.inv2dxi), i2deta = T(cv.inv2deta);
   const T ceta_unit = T(cv.c / cv.H);
-  const T xeH = T(a.geo.xeH[goff + cc]);             // x_eta / H of this column
+  const T xeH = GEN ? T(0) : T(a.geo.xeH[goff + cc]);  // x_eta / H of this column
+  // general quadrilateral (bilinear map): x_eta, y_eta of this column and
+  // x_xi, y_xi of a row; the node's metrics follow from Eqs. (3.2)-(3.3)
+  const T gxe = GEN ? T(a.geo.qxeta_f[goff + cc]) : T(0);
+  const T gye = GEN ? T(a.geo.qyeta_f[goff + cc]) : T(0);
+  auto row_xxi = [&](int j) -> T { return a.geo.qxxi_f[goff + j]; };
+  auto row_yxi = [&](int j) -> T { return a.geo.qyxi_f[goff + j]; };
   const T wx = T(((c == 0 || c == nx - 1) ? 0.5 : 1.0) * cv.dxi);
   const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
@@ -320,7 +360,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   // metrics of this iteration's half-step and full-step rows, loaded one
   // iteration ahead (rows clamped into the cavity; unused outside it)
   auto crow = [&](int r) { return min(max(r, 0), ny - 1); };
-  T A1 = row_cxix(crow(kb - 2 + h)), A2 = row_cxix(crow(kb - 4 + h)), J2 = row_jac(crow(kb - 4 + h));
+  // (general quadrilaterals load their row values where they are used: one
+  // broadcast load per warp, which keeps the register budget of the march)
+  T A1 = 0, A2 = 0, J2 = 0;
+  if constexpr (!GEN) {
+    A1 = row_cxix(crow(kb - 2 + h)), A2 = row_cxix(crow(kb - 4 + h)), J2 = row_jac(crow(kb - 4 + h));
+  }
 
   for (int it = 0; it < nit; ++it) {
     const int k = kb + 2 * it;
@@ -358,16 +403,24 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     const bool do1 = m >= mlo && m <= mhi;
     if (do1 && inner_c && l >= 2 && l < NC - 2) {
       const int sm = slot6(m);
-      const T A = A1;                                  // c xi_x of row m
-      const T B = A * xeH;                             // c xi_x x_eta / H
       const bool lo = m == 1, hi = m == ny - 2;
       T fbar[9];
       fbar[0] = S.fb[sm][0][l];
       {
         const T *cols[5] = {&S.fb[slot6(m - 2)][0][l], &S.fb[slot6(m - 1)][0][l], &S.fb[sm][0][l],
                             &S.fb[slot6(m + 1)][0][l], &S.fb[slot6(m + 2)][0][l]};
-        AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
-                                     eta_b, i2dxi, i2deta, hdt, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
+        if constexpr (GEN) {
+          const T X = row_xxi(m), Y = row_yxi(m);
+          const T iJ = c_ / (X * gye - gxe * Y);         // c / J of node (c, m)
+          AdvectAllGen<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
+                                          iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, hdt,
+                                          &S.fb[sm][0][l], fbar);  // Eq. (3.7)
+        } else {
+          const T A = A1;                                // c xi_x of row m
+          const T B = A * xeH;                           // c xi_x x_eta / H
+          AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
+                                       eta_b, i2dxi, i2deta, hdt, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
+        }
       }
       T ux, uy, P;
       moments(fbar, c_, cs2, ux, uy, P);
@@ -398,7 +451,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         T F[9];
 #pragma unroll
         for (int q = 0; q < 9; ++q) F[q] = S.fh[src][q][ln];
-        nee(F, (lid && inner_c) ? Uw : T(0), T(0), c_, cs2, ics2);
+        nee(F, (lid && inner_c) ? Uw : T(0), (lid && inner_c) ? Uwy : T(0), c_, cs2, ics2);
 #pragma unroll
         for (int q = 0; q < 9; ++q) S.fh[dst][q][l] = F[q];
       }
@@ -413,15 +466,23 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     T gnv[9];
     if (do2 && inner_c && l >= 4 && l < NC - 4) {
       const int so = slot6(o);
-      const T A = A2;                                  // c xi_x of row o
-      const T B = A * xeH;
       const bool lo = o == 1, hi = o == ny - 2;
       gnv[0] = S.sf[sp][0][t];
       {
         const T *cols[5] = {&S.fh[slot6(o - 2)][0][l], &S.fh[slot6(o - 1)][0][l], &S.fh[so][0][l],
                             &S.fh[slot6(o + 1)][0][l], &S.fh[slot6(o + 2)][0][l]};
-        AdvectAll<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
-                                     eta_b, i2dxi, i2deta, dt, &S.sf[sp][0][t], gnv);  // Eq. (3.6)
+        if constexpr (GEN) {
+          const T X = row_xxi(o), Y = row_yxi(o);
+          const T iJ = c_ / (X * gye - gxe * Y);         // c / J of node (c, o)
+          AdvectAllGen<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
+                                          iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, dt,
+                                          &S.sf[sp][0][t], gnv);  // Eq. (3.6)
+        } else {
+          const T A = A2;                                // c xi_x of row o
+          const T B = A * xeH;
+          AdvectAll<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
+                                       eta_b, i2dxi, i2deta, dt, &S.sf[sp][0][t], gnv);  // Eq. (3.6)
+        }
       }
       if (clo || chi) {                                // values the wall columns extrapolate
 #pragma unroll
@@ -430,10 +491,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     }
     if (in_a(row_of(it + 1))) take(collide(it + 1, lp_next));  // lambda of the next row
     lp_next = lam_load(row_of(it + 2));
-    const T J2o = J2;                                // Jacobian of row o
-    A1 = row_cxix(crow(m + 2));
-    A2 = row_cxix(crow(o + 2));
-    J2 = row_jac(crow(o + 2));
+    [[maybe_unused]] const T J2o = J2;               // Jacobian of row o (trapezoid)
+    if constexpr (!GEN) {
+      A1 = row_cxix(crow(m + 2));
+      A2 = row_cxix(crow(o + 2));
+      J2 = row_jac(crow(o + 2));
+    }
     __syncthreads();  // f-hat(t + dt) of columns 1 and nx-2
 
     if (do2 && own) {
@@ -453,7 +516,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 #pragma unroll
         for (int q = 0; q < 9; ++q) fpo[q] = S.sf[sp][q][t];
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
-        const T wJ = wx * wy_in * J2o;
+        T Jo;
+        if constexpr (GEN)
+          Jo = row_xxi(o) * gye - gxe * row_yxi(o);    // Jacobian of node (c, o)
+        else
+          Jo = J2o;
+        const T wJ = wx * wy_in * Jo;
         leaf_add(leaf, p, ux, uy, P, u0, v0, P0, Pr, wJ, a.status);
       }
       // wall rows produced with their neighbour rows
@@ -469,7 +537,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
 #pragma unroll
           for (int q = 0; q < 9; ++q) F[q] = gnv[q];
         }
-        nee(F, (top && inner_c) ? Uw : T(0), T(0), c_, cs2, ics2);
+        nee(F, (top && inner_c) ? Uw : T(0), (top && inner_c) ? Uwy : T(0), c_, cs2, ics2);
         const int r = bottom ? 0 : ny - 1;
         const int64_t nd = int64_t(r) * pitch + c;
 #pragma unroll
@@ -478,7 +546,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
           T wx2, wy2, wP2;
           moments(F, c_, cs2, wx2, wy2, wP2);
           const int e = bottom ? 0 : 1;
-          const T wJ = wx * wy_edge * row_jac(r);
+          T Jr;
+          if constexpr (GEN)
+            Jr = row_xxi(r) * gye - gxe * row_yxi(r);
+          else
+            Jr = row_jac(r);
+          const T wJ = wx * wy_edge * Jr;
           leaf_add(leaf, p, wx2, wy2, wP2, S.edge[e][0][l], S.edge[e][1][l], S.edge[e][2][l], Pr,
                    wJ, a.status);
         }
@@ -521,13 +594,13 @@ struct Occ {
 // blockIdx.x, blockIdx.x + gridDim.x, ... of the largest-first order;
 // 2 persistent CTAs taking positions from an atomic counter (no waiting on
 // other CTAs: a CTA that finds the list exhausted returns).
-template <class T, int NT, bool IMPL>
+template <class T, int NT, bool IMPL, bool GEN>
 __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
   __shared__ int next;
   if (a.schedule == 0) {
-    fused_task<T, NT, IMPL>(a, S, blockIdx.x);
+    fused_task<T, NT, IMPL, GEN>(a, S, blockIdx.x);
     return;
   }
   for (int it = 0;; ++it) {
@@ -541,15 +614,15 @@ __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
       __syncthreads();
     }
     if (pos >= a.ntasks) return;
-    fused_task<T, NT, IMPL>(a, S, a.order[pos]);
+    fused_task<T, NT, IMPL, GEN>(a, S, a.order[pos]);
   }
 }
 
-template <class T, int NT, bool IMPL>
+template <class T, int NT, bool IMPL, bool GEN = false>
 static void configure_nt() {
   static bool configured = false;  // the attribute is per function
   if (!configured) {
-    cudaFuncSetAttribute(k_fused<T, NT, IMPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fused<T, NT, IMPL, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(FusedSmem<T, NT>)));
     configured = true;
   }
@@ -557,12 +630,21 @@ static void configure_nt() {
 
 template <class T, int NT>
 static void launch_fused_nt(const FusedArgs &a, int grid, cudaStream_t s) {
+  // general quadrilaterals: FP32 with the lagged relaxation time only (the
+  // host admits no other combination)
+  if constexpr (sizeof(T) == 4) {
+    if (a.general) {
+      configure_nt<T, NT, false, true>();
+      k_fused<T, NT, false, true><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+      return;
+    }
+  }
   if (a.implicit) {
     configure_nt<T, NT, true>();
-    k_fused<T, NT, true><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+    k_fused<T, NT, true, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
   } else {
     configure_nt<T, NT, false>();
-    k_fused<T, NT, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+    k_fused<T, NT, false, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
   }
 }
 
@@ -570,7 +652,7 @@ template <class T, int NT>
 static int blocks_per_sm_nt() {
   configure_nt<T, NT, false>();
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false>, NT,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false, false>, NT,
                                                 int(sizeof(FusedSmem<T, NT>)));
   return n;
 }

@@ -48,6 +48,10 @@ struct Geo {
   // general quadrilaterals (staged kernels): per node, at 7 * off + k * plane,
   // k = 0..6: xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J (Eqs. 3.2-3.3)
   const double *gmet;
+  // general quadrilaterals (fused FP32 kernel): the bilinear map's separable
+  // derivatives as floats, at goff: x_xi(eta_j), y_xi(eta_j) (ny entries),
+  // x_eta(xi_i), y_eta(xi_i) (nx entries)
+  const float *qxxi_f, *qyxi_f, *qxeta_f, *qyeta_f;
 };
 
 // Device buffers of a handle. T is double (FP64) or float (FP32DEV).
@@ -111,6 +115,7 @@ struct FusedArgs {
   const double *pref;  // [ncav] reference pressure of the stored deviations
   int *cav_done;       // [ncav] tasks of the step finished (zero between steps)
   int implicit;        // 1: implicit form of Eq. (2.14) (kernel variant), 0: lagged
+  int general;         // 1: general quadrilaterals (kernel variant; FP32, lagged)
   double *resid;       // [ncav][4] residual outputs (formed by each cavity's last task)
   int want_residual;
 };

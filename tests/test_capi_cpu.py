@@ -116,7 +116,7 @@ def test_invalid_quadrilaterals_rejected_before_device_use(lib, corners, kw, fra
     assert frag in str(e.value)
 
 
-@pytest.mark.parametrize("field,val,frag", [("kernel", 2, "staged kernels"),
+@pytest.mark.parametrize("field,val,frag", [("kernel", 2, "fused kernel needs FP32DEV"),
                                             ("dt_mode", 0, "dt_mode GRID")])
 def test_quadrilateral_options_rejected(lib, field, val, frag):
     from paper_2306_07603_gb300 import capi

@@ -107,14 +107,25 @@ def test_batch_of_two_quadrilaterals_from_rest_with_fields():
         assert np.abs(P - d["P"]).max() <= 1e-12 * max(np.abs(d["P"]).max(), 1e-3)
 
 
-def test_fp32_deviation_one_step_error_on_a_quadrilateral():
-    run = O.quad_run(37, 29, SKEW, 400.0, 0.75)
+FP32_KERNELS = {
+    "staged": dict(kernel="staged"),
+    "fused64x8": dict(kernel="fused", fused_threads=64, fused_rows=8),
+    "fused128": dict(kernel="fused", fused_threads=128),
+    "fused256x16": dict(kernel="fused", fused_threads=256, fused_rows=16),
+}
+
+
+@pytest.mark.parametrize("kname", list(FP32_KERNELS))
+@pytest.mark.parametrize("nx,ny,corners,Re,n", [(37, 29, SKEW, 400.0, 0.75),
+                                                (70, 9, KITE, 100.0, 1.5)])
+def test_fp32_deviation_one_step_error_on_a_quadrilateral(nx, ny, corners, Re, n, kname):
+    """FP32 deviation storage on a quadrilateral, staged and fused (the fused
+    kernel's general variant: metrics of the bilinear map per node in FP32)."""
+    run = O.quad_run(nx, ny, corners, Re, n)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     fo, lo = O.step(f0, l0, run.g, run.prm)
-    s = quad_solver([(37, 29, SKEW, 400.0, 0.75)], precision="fp32dev")
-    from paper_2306_07603_gb300 import capi
-    assert s.info(0).kernel == capi.IFDLBM_KERNEL_STAGED   # AUTO selects the staged kernels
+    s = quad_solver([(nx, ny, corners, Re, n)], precision="fp32dev", **FP32_KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)
@@ -122,6 +133,58 @@ def test_fp32_deviation_one_step_error_on_a_quadrilateral():
     uo, vo, Po = O.macros(fo)
     assert rel(ug, uo) < 1e-5 and rel(vg, vo) < 1e-5 and rel(Pg, Po) < 1e-4
     assert rel(lg, lo) < 1e-5
+    r = s.residual()[0]
+    Ek = O.kinetic_energy(*O.macros(fo)[:2], run.g)
+    assert abs(r[3] - Ek) <= 1e-5 * Ek
+
+
+def test_kernel_choice_for_quadrilaterals():
+    from paper_2306_07603_gb300 import capi
+    spec = [(17, 17, SKEW, 100.0, 0.75)]
+    assert quad_solver(spec, precision="fp32dev").info(0).kernel == capi.IFDLBM_KERNEL_FUSED
+    assert quad_solver(spec).info(0).kernel == capi.IFDLBM_KERNEL_STAGED            # FP64
+    assert (quad_solver(spec, precision="fp32dev", lambda_mode="implicit").info(0).kernel
+            == capi.IFDLBM_KERNEL_STAGED)
+
+
+def test_fused_fp32_tracks_staged_fp32_over_many_steps():
+    """A batch of three quadrilaterals (ragged tails, a 9-row grid) from an
+    oracle state, 300 steps in FP32 on the fused and on the staged kernels:
+    the two FP32 trajectories stay within FP32 rounding of each other."""
+    specs = [(37, 29, SKEW, 400.0, 0.75), (41, 33, KITE, 100.0, 1.5), (70, 9, SKEW, 100.0, 0.5)]
+    runs = []
+    for nx, ny, cr, Re, n in specs:
+        r = O.quad_run(nx, ny, cr, Re, n)
+        r.advance(40)
+        runs.append(r)
+    out = {}
+    for kname in ("staged", "fused64x8"):
+        s = quad_solver(specs, precision="fp32dev", **FP32_KERNELS[kname])
+        for k, r in enumerate(runs):
+            s.set_state(k, r.fhat, r.lam)
+        s.step(300)
+        out[kname] = [s.macros(k) for k in range(len(specs))]
+        s.close()
+    for k in range(len(specs)):
+        a, b = out["staged"][k], out["fused64x8"][k]
+        umax = np.sqrt(a["u"] ** 2 + a["v"] ** 2).max()
+        for key in ("u", "v"):
+            assert np.abs(a[key] - b[key]).max() <= 1e-5 * umax, (k, key)
+        assert rel(b["psi"], a["psi"]) <= 1e-5, k
+
+
+def test_trapezoid_corners_fused_fp32_equal_the_trapezoid_handle():
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    a = quad_solver([(65, 49, _trapezoid_corners(), 400.0, 0.75)], precision="fp32dev",
+                    kernel="fused", fused_threads=128)
+    b = Solver([cavity(65, 49, 400.0, 0.75, theta_deg=60.0)], precision="fp32dev",
+               kernel="fused", fused_threads=128)
+    a.step(100)
+    b.step(100)
+    ma, mb = a.macros(0), b.macros(0)
+    umax = np.sqrt(mb["u"] ** 2 + mb["v"] ** 2).max()
+    for key in ("u", "v"):
+        assert np.abs(ma[key] - mb[key]).max() <= 1e-5 * umax, key
 
 
 def test_eddies_of_a_developed_flow_are_mapped_through_the_corners():
