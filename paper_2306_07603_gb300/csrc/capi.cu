@@ -385,25 +385,6 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
 
 namespace {
 
-// Metrics of the bilinear map of a general quadrilateral at (xi, eta),
-// Eqs. (3.2)-(3.3): m = xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J.
-void quad_node_metrics(const double *cr, double xi, double eta, double m[7]) {
-  const double x0 = cr[0], y0 = cr[1], x1 = cr[2], y1 = cr[3], x2 = cr[4], y2 = cr[5],
-               x3 = cr[6], y3 = cr[7];
-  const double x_xi = (1 - eta) * (x1 - x0) + eta * (x3 - x2);
-  const double y_xi = (1 - eta) * (y1 - y0) + eta * (y3 - y2);
-  const double x_eta = (1 - xi) * (x2 - x0) + xi * (x3 - x1);
-  const double y_eta = (1 - xi) * (y2 - y0) + xi * (y3 - y1);
-  const double J = x_xi * y_eta - x_eta * y_xi;
-  m[0] = y_eta / J;
-  m[1] = -x_eta / J;
-  m[2] = -y_xi / J;
-  m[3] = x_xi / J;
-  m[4] = x_eta;
-  m[5] = y_eta;
-  m[6] = J;
-}
-
 int validate_quad(ifdlbm_ctx *h, int idx, const ifdlbm_quad_cavity &q) {
   char buf[256];
   auto bad = [&](const char *what) {
@@ -417,7 +398,7 @@ int validate_quad(ifdlbm_ctx *h, int idx, const ifdlbm_quad_cavity &q) {
   for (double xi : {0.0, 1.0})
     for (double eta : {0.0, 1.0}) {
       double m[7];
-      quad_node_metrics(q.corners, xi, eta, m);
+      ifd::quad_node_metrics(q.corners, xi, eta, m);
       if (!(m[6] > 0)) return bad("corners must make a convex, counter-clockwise quadrilateral");
     }
   const double tl = std::hypot(q.corners[6] - q.corners[4], q.corners[7] - q.corners[5]);
@@ -507,7 +488,6 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->cav.resize(ncav);
   h->courant.resize(ncav);
   std::vector<double> xix, xeH, xxi, xeta;
-  std::vector<double> gmet_h;  // per-node metric planes of general quadrilaterals
   for (int k = 0; k < ncav; ++k) {
     const ifdlbm_cavity &s = cavs[k];
     CavDev &cv = h->cav[k];
@@ -535,35 +515,34 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     cv.implicit = opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
-    if (quads) gmet_h.resize(7 * size_t(off));
     cv.general = quads ? 1 : 0;
     cv.lid_ux = s.U_lid;
     cv.lid_uy = 0.0;
     if (quads) {
-      // per-node metric planes; the lid moves along the top edge (corner 2 to 3)
+      // the lid moves along the top edge (corner 2 to 3); the per-node metric
+      // planes are formed on the device (launch_quad_metrics)
       const double *cr = quads[k].corners;
       const double tl = std::hypot(cr[6] - cr[4], cr[7] - cr[5]);
       cv.lid_ux = s.U_lid * (cr[6] - cr[4]) / tl;
       cv.lid_uy = s.U_lid * (cr[7] - cr[5]) / tl;
-      for (int j = 0; j < s.ny; ++j)
-        for (int i = 0; i < s.nx; ++i) {
-          double m[7];
-          quad_node_metrics(cr, double(i) / (s.nx - 1), double(j) / (s.ny - 1), m);
-          const int64_t node = int64_t(j) * cv.pitch + i;
-          for (int t = 0; t < 7; ++t) gmet_h[7 * cv.off + t * cv.plane + node] = m[t];
-        }
     }
     if (quads && opt.dt <= 0) {
-      // CFL on the contravariant speeds of Eq. (3.4), maxima over all nodes
+      // CFL on the contravariant speeds of Eq. (3.4), maxima over all nodes.
+      // For the bilinear map c_xi = c (e_x y_eta - e_y x_eta) / J and
+      // c_eta = c (e_y x_xi - e_x y_xi) / J, with x_xi, y_xi functions of eta
+      // only, x_eta, y_eta of xi only and J > 0 linear in each coordinate: along
+      // every grid line each is a ratio of linear functions, monotonic, so the
+      // maxima of |c_xi| and |c_eta| sit at the four corner nodes.
       double mxi = 0.0, meta = 0.0;
-      for (int j = 0; j < s.ny; ++j)
-        for (int i = 0; i < s.nx; ++i) {
-          const double *m = &gmet_h[7 * cv.off + int64_t(j) * cv.pitch + i];
+      for (double xi : {0.0, 1.0})
+        for (double eta : {0.0, 1.0}) {
+          double m[7];
+          ifd::quad_node_metrics(quads[k].corners, xi, eta, m);
           for (int q = 1; q < 9; ++q) {
             static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
             static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-            mxi = std::max(mxi, std::fabs(opt.c * (EX[q] * m[0] + EY[q] * m[cv.plane])));
-            meta = std::max(meta, std::fabs(opt.c * (EX[q] * m[2 * cv.plane] + EY[q] * m[3 * cv.plane])));
+            mxi = std::max(mxi, std::fabs(opt.c * (EX[q] * m[0] + EY[q] * m[1])));
+            meta = std::max(meta, std::fabs(opt.c * (EX[q] * m[2] + EY[q] * m[3])));
           }
         }
       cv.dt = opt.cfl * std::min((1.0 / (s.nx - 1)) / mxi, (1.0 / (s.ny - 1)) / meta);
@@ -617,16 +596,21 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
       xeta[cv.goff + i] = x_eta;
       xeH[cv.goff + i] = x_eta / H;
     }
-    for (int j = 0; j < s.ny; ++j)
-      for (int i = 0; i < s.nx; i += quads ? 1 : std::max(1, s.nx - 1))
+    // (general quadrilaterals: dt (|c_xi| / dxi + |c_eta| / deta) is, along
+    // each grid line, a ratio of piecewise linear functions to a positive
+    // linear one, largest at an end: the corner nodes suffice)
+    for (int j = 0; j < s.ny; j += quads ? std::max(1, s.ny - 1) : 1)
+      for (int i = 0; i < s.nx; i += std::max(1, s.nx - 1))
         for (int q = 1; q < 9; ++q) {
           static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
           static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
           double cxi, ceta;
           if (quads) {
-            const double *m = &gmet_h[7 * cv.off + int64_t(j) * cv.pitch + i];
-            cxi = opt.c * (EX[q] * m[0] + EY[q] * m[cv.plane]);
-            ceta = opt.c * (EX[q] * m[2 * cv.plane] + EY[q] * m[3 * cv.plane]);
+            double m[7];
+            ifd::quad_node_metrics(quads[k].corners, double(i) / (s.nx - 1), double(j) / (s.ny - 1),
+                                   m);
+            cxi = opt.c * (EX[q] * m[0] + EY[q] * m[1]);
+            ceta = opt.c * (EX[q] * m[2] + EY[q] * m[3]);
           } else {
             const double A = opt.c * xix[cv.goff + j];
             cxi = A * (EX[q] - EY[q] * xeH[cv.goff + i]);
@@ -681,7 +665,9 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
   double *gmet = nullptr;
   float *qsep = nullptr;  // x_xi, y_xi, x_eta, y_eta of the bilinear maps (fused FP32 kernel)
-  if (quads) ok &= (gmet = (double *)A(gmet_h.size() * sizeof(double))) != nullptr;
+  double *qcorners = nullptr;
+  if (quads) ok &= (gmet = (double *)A(size_t(7 * off) * sizeof(double))) != nullptr;
+  if (quads) ok &= (qcorners = (double *)A(size_t(8 * ncav) * sizeof(double))) != nullptr;
   if (quads) ok &= (qsep = (float *)A(size_t(4 * goff) * sizeof(float))) != nullptr;
   if (!ok) {
     release_all(h);
@@ -734,8 +720,8 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   cudaStream_t s = h->stream;
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
                          geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
-                         ifd::POW_TABLE_SIZE * sizeof(double) + gmet_h.size() * sizeof(double) +
-                         qsep_h.size() * sizeof(float));
+                         ifd::POW_TABLE_SIZE * sizeof(double) + qsep_h.size() * sizeof(float) +
+                         (quads ? size_t(8 * ncav) * sizeof(double) : 0));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
                       cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -746,9 +732,20 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(geof, geof_h.data(), geof_h.size() * sizeof(float), cudaMemcpyHostToDevice,
                         s);
-  if (gmet && e == cudaSuccess)
-    e = cudaMemcpyAsync(gmet, gmet_h.data(), gmet_h.size() * sizeof(double),
+  std::vector<double> qcorners_h;
+  for (int k = 0; quads && k < ncav; ++k)
+    qcorners_h.insert(qcorners_h.end(), quads[k].corners, quads[k].corners + 8);
+  if (qcorners && e == cudaSuccess)
+    e = cudaMemcpyAsync(qcorners, qcorners_h.data(), qcorners_h.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s);
+  if (gmet && e == cudaSuccess) {
+    e = cudaMemsetAsync(gmet, 0, size_t(7 * off) * sizeof(double), s);  // row padding too
+    if (e == cudaSuccess) {
+      ifd::launch_quad_metrics(h->b.cav, ncav, h->max_n2, qcorners, gmet, s);
+      g_launches += 1;
+      e = cudaGetLastError();
+    }
+  }
   if (qsep && e == cudaSuccess)
     e = cudaMemcpyAsync(qsep, qsep_h.data(), qsep_h.size() * sizeof(float),
                         cudaMemcpyHostToDevice, s);

@@ -157,6 +157,30 @@ void launch_adjoint_step(const AdjArgs &a, int ntiles, int ncav, double *dparams
 // Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
 void fill_pow_tables(double *tab);
 void launch_pow_f32_selftest(int n, const double *x, double m, double *out, cudaStream_t s);
+
+// Metrics of the bilinear map of a general quadrilateral at (xi, eta),
+// Eqs. (3.2)-(3.3), from its corners cr = {x0, y0, x1, y1, x2, y2, x3, y3}
+// (bottom-left, bottom-right, top-left, top-right):
+// m = xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J.
+__host__ __device__ inline void quad_node_metrics(const double *cr, double xi, double eta,
+                                                  double m[7]) {
+  const double x_xi = (1 - eta) * (cr[2] - cr[0]) + eta * (cr[6] - cr[4]);
+  const double y_xi = (1 - eta) * (cr[3] - cr[1]) + eta * (cr[7] - cr[5]);
+  const double x_eta = (1 - xi) * (cr[4] - cr[0]) + xi * (cr[6] - cr[2]);
+  const double y_eta = (1 - xi) * (cr[5] - cr[1]) + xi * (cr[7] - cr[3]);
+  const double J = x_xi * y_eta - x_eta * y_xi;
+  m[0] = y_eta / J;
+  m[1] = -x_eta / J;
+  m[2] = -y_xi / J;
+  m[3] = x_xi / J;
+  m[4] = x_eta;
+  m[5] = y_eta;
+  m[6] = J;
+}
+// Per-node metric planes (Geo::gmet) of every cavity of a quadrilateral
+// handle, from corners [ncav][8]; max_n2 = the largest nx * ny.
+void launch_quad_metrics(const CavDev *cav, int ncav, int64_t max_n2, const double *corners,
+                         double *gmet, cudaStream_t s);
 void launch_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
                          double *ref, cudaStream_t s);
 

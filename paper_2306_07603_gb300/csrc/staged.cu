@@ -462,6 +462,27 @@ __global__ void k_pow_f32_selftest(int n, const double *x, double m, double *out
   out[k] = double(pow_f32(float(x[k]), float(m)));
 }
 
+// Per-node metric planes of the general quadrilaterals, one thread per node
+// (blockIdx.y = cavity).
+__global__ void k_quad_metrics(const CavDev *cavs, const double *corners, double *gmet) {
+  const CavDev &cv = cavs[blockIdx.y];
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= int64_t(cv.nx) * cv.ny) return;
+  const int j = int(n / cv.nx), i = int(n - int64_t(j) * cv.nx);
+  double m[7];
+  quad_node_metrics(corners + 8 * blockIdx.y, double(i) / (cv.nx - 1), double(j) / (cv.ny - 1), m);
+  double *gm = gmet + 7 * cv.off;
+  const int64_t node = int64_t(j) * cv.pitch + i;
+#pragma unroll
+  for (int t = 0; t < 7; ++t) gm[t * cv.plane + node] = m[t];
+}
+
+void launch_quad_metrics(const CavDev *cav, int ncav, int64_t max_n2, const double *corners,
+                         double *gmet, cudaStream_t s) {
+  const dim3 grid(unsigned((max_n2 + 255) / 256), unsigned(ncav));
+  k_quad_metrics<<<grid, 256, 0, s>>>(cav, corners, gmet);
+}
+
 void launch_pow_f32_selftest(int n, const double *x, double m, double *out, cudaStream_t s) {
   k_pow_f32_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, out);
 }

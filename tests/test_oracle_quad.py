@@ -93,3 +93,23 @@ def test_lid_moves_along_the_top_edge():
     t = np.array([x3 - x2, y3 - y2]) / math.hypot(x3 - x2, y3 - y2)
     assert np.allclose(ux[1:-1], 0.1 * t[0]) and np.allclose(uy[1:-1], 0.1 * t[1])
     assert ux[0] == ux[-1] == uy[0] == uy[-1] == 0.0
+
+
+def test_contravariant_speed_maxima_sit_at_the_corners():
+    """The library takes dt and the Courant number of a quadrilateral from its
+    four corner nodes: along every grid line of the bilinear map c_xi and
+    c_eta are ratios of linear functions to the positive, linear J, so
+    max|c_xi|, max|c_eta| and max(|c_xi|/dxi + |c_eta|/deta) over the grid
+    are attained at corners. Checked over every node of seeded quadrilaterals."""
+    rng = np.random.default_rng(7)
+    for _ in range(20):
+        d = rng.uniform(-0.25, 0.25, size=(4, 2))
+        corners = tuple((x0 + d[k, 0], y0 + d[k, 1])
+                        for k, (x0, y0) in enumerate(((0, 0), (1, 0), (0, 1), (1, 1))))
+        g = O.quad_grid(31, 23, corners)
+        axi, aeta = np.abs(g.cxi), np.abs(g.ceta)
+        cfl = axi / g.dxi + aeta / g.deta
+        for a in (axi, aeta, cfl):
+            full = a.max()
+            at_corners = max(a[:, j, i].max() for j in (0, -1) for i in (0, -1))
+            assert at_corners >= full * (1 - 1e-14)
