@@ -22,6 +22,11 @@ lid-driven isosceles trapezoidal cavity mapped to the unit square:
 * calculation process Steps (1)-(8) ................... Sec. 4
 * global relative error ............................... Eq. (2.19)
 * kinetic energy ...................................... Eq. (5.1)
+* eddy centres of Tables 1-3 .......................... Sec. 5.1 (a READING)
+* implicit relaxation time (Eq. 2.14 at the current
+  lambda, solved by bisection) ........................ Eq. (2.14), (2.18)
+* general convex quadrilaterals (bilinear map,
+  per-node metrics) ................................... Eqs. (3.2)-(3.4) (a READING)
 
 Where the paper is silent, garbled or self-contradictory, one explicit
 reading is taken; each is marked ``READING`` below. The same readings bind
