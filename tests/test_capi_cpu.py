@@ -128,3 +128,37 @@ def test_quadrilateral_options_rejected(lib, field, val, frag):
         capi.ifdlbm_create_quad_batch([quad_cavity(9, 9, SKEW, 100.0, 0.75)], o)
     assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG
     assert frag in str(e.value)
+
+
+STRUCTS = ["ifdlbm_geometry", "ifdlbm_options", "ifdlbm_cavity", "ifdlbm_quad_cavity",
+           "ifdlbm_info_t", "ifdlbm_tuning", "ifdlbm_eddy"]
+
+
+def test_header_is_plain_c_and_the_binding_matches_its_layouts(tmp_path):
+    """The ABI header compiles as C99, and every struct's size and field
+    offsets in the ctypes binding equal the C compiler's."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import subprocess
+
+    from paper_2306_07603_gb300 import capi
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ifdlbm.h"', "int main(void) {"]
+    expect = []
+    for name in STRUCTS:
+        cls = getattr(capi, name)
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        expect.append(ctypes.sizeof(cls))
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {fname}));')
+            expect.append(getattr(cls, fname).offset)
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == expect
