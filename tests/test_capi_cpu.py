@@ -162,3 +162,44 @@ def test_header_is_plain_c_and_the_binding_matches_its_layouts(tmp_path):
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
                                           check=True).stdout.split()]
     assert got == expect
+
+
+def test_library_is_usable_from_c(lib, tmp_path):
+    """A C program links libifdlbm.so and calls it through the header alone:
+    options, argument checks, and create (IFDLBM_ERR_CUDA without a GPU; on a
+    GPU one step, a residual read and destroy)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    import subprocess
+
+    from paper_2306_07603_gb300 import capi
+    src = tmp_path / "use.c"
+    src.write_text(r'''
+#include <stdio.h>
+#include "ifdlbm.h"
+int main(void) {
+  ifdlbm_options o;
+  if (ifdlbm_default_options(&o) != IFDLBM_OK || o.cfl != 0.5) return 10;
+  ifdlbm_geometry g = {1.0, 1.0, 60.0};
+  ifdlbm_handle h = 0;
+  if (ifdlbm_create(3, 9, g, 100.0, 0.75, 0.1, &o, NULL, &h) != IFDLBM_ERR_INVALID_ARG) return 11;
+  int rc = ifdlbm_create(17, 17, g, 100.0, 0.75, 0.1, &o, NULL, &h);
+  if (rc == IFDLBM_ERR_CUDA) { printf("nogpu %s\n", ifdlbm_last_error(NULL)); return 0; }
+  if (rc != IFDLBM_OK) return 12;
+  double r[4];
+  if (ifdlbm_step(h, 2) != IFDLBM_OK || ifdlbm_residual(h, r) != IFDLBM_OK) return 13;
+  ifdlbm_destroy(h);
+  printf("gpu %g\n", r[3]);
+  return 0;
+}
+''')
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(capi.LIB_PATH)
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", libdir, "-lifdlbm",
+                        f"-Wl,-rpath,{libdir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, (out.returncode, out.stdout, out.stderr)
+    assert out.stdout.startswith(("nogpu", "gpu"))
