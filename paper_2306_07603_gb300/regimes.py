@@ -57,8 +57,10 @@ def record(specs, precision="fp32dev", transient=1_000_000, steps=1_000_000, eve
     import torch
 
     from . import capi
-    from .solver import Solver, cavity
-    s = Solver([cavity(c.nx, c.ny, c.Re, c.n, theta_deg=c.theta_deg, U_lid=c.U_lid, L=c.L, H=c.H)
+    from .solver import Solver, cavity, quad_cavity
+    s = Solver([quad_cavity(c.nx, c.ny, c.corners, c.Re, c.n, U_lid=c.U_lid, H=c.H)
+                if hasattr(c, "corners") else
+                cavity(c.nx, c.ny, c.Re, c.n, theta_deg=c.theta_deg, U_lid=c.U_lid, L=c.L, H=c.H)
                 for c in specs], precision=precision, **opts)
     idx = [(k, int(round(xi * (c.nx - 1))), int(round(eta * (c.ny - 1))))
            for k, c in enumerate(specs) for (xi, eta) in probes]
@@ -142,7 +144,8 @@ def summarize(specs, rec, probes=PROBES, **kw):
         cl = classify(E, dts, **kw)
         pr = rec["probes"][:, k]
         rows.append({
-            "grid": f"{c.nx}x{c.ny}", "theta": c.theta_deg, "n": c.n, "Re": c.Re,
+            "grid": f"{c.nx}x{c.ny}", "theta": getattr(c, "theta_deg", None),
+            "corners": getattr(c, "corners", None), "n": c.n, "Re": c.Re,
             "E_mean": float(E.mean()), "E_var": float(E.var()), **cl,
             "probes": [{"xi": xi, "eta": eta, "u_mean": float(pr[:, q, 0].mean()),
                         "u_var": float(pr[:, q, 0].var()), "v_mean": float(pr[:, q, 1].mean()),
