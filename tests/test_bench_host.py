@@ -79,3 +79,15 @@ def test_quad_workload_cavities_are_convex_and_seeded():
     for sp in a:
         g = O.quad_grid(9, 9, sp.corners)      # raises unless J > 0 everywhere
         assert g.J.min() > 0.3
+
+
+def test_oracle_pool_runs_every_cavity_on_several_processes():
+    """The reference arm's oracle pool: spawned single-threaded processes, each
+    advancing its group of cavities; whole-job throughput over all of them."""
+    import bench
+    from paper_2306_07603_gb300.workloads import CavitySpec
+    specs = [CavitySpec(17, 17, 100.0, 0.75, 60.0), CavitySpec(21, 17, 400.0, 1.25, 45.0),
+             CavitySpec(17, 23, 100.0, 1.0, 90.0)]
+    mlups, wall, used = bench.oracle_pool_mlups(specs, 1, 3, 2)
+    assert used == 2 and wall > 0 and mlups > 0
+    assert mlups == pytest.approx(sum(sp.nodes for sp in specs) * 3 / wall / 1e6)
