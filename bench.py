@@ -62,6 +62,9 @@ def parse_args(argv=None):
     p.add_argument("--kernel", default="auto", choices=["auto", "staged", "fused"])
     p.add_argument("--lambda-mode", default="lagged", choices=["lagged", "implicit"],
                    help="relaxation time of Eq. (2.14): lagged (the paper's) or implicit")
+    p.add_argument("--power-fp32", action="store_true",
+                   help="fp32dev opt-in: power law of Eq. (1.4) in FP32 (outside the FP32 "
+                        "deviation form, which keeps it in FP64)")
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -366,6 +369,7 @@ def cpu_baseline(specs, seconds):
 # The GPU arm
 # ---------------------------------------------------------------------------
 LAMBDA_MODE = "lagged"  # set from --lambda-mode
+POWER_FP32 = False      # set from --power-fp32
 
 
 def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
@@ -380,6 +384,8 @@ def make_solver(specs, precision, kernel, stream=None, workload=None, **extra):
     opts = dict(WORKLOAD_OPTIONS.get(workload, {}), **extra)
     if LAMBDA_MODE != "lagged":
         opts["lambda_mode"] = LAMBDA_MODE
+    if POWER_FP32:
+        opts["power_fp32"] = True
     return Solver(cavs, stream=stream, precision=precision, kernel=kernel, **opts)
 
 
@@ -506,7 +512,7 @@ def run_ours(args):
         roofline = {"bound": "hbm", "kernel": DEVICE_KERNEL[dom], "achieved": round(achieved, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                     "traffic": traffic_per_launch(dom, args.precision, lu_step, args.workload)
-                    if args.lambda_mode == "lagged" else None,
+                    if args.lambda_mode == "lagged" and not args.power_fp32 else None,
                     "algorithmic_bytes": algo, "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)"
                     if peak_src == "measured" else "fallback",
                     "time_share": round(ms / sum(v[0] for v in kern.values()), 4)}
@@ -516,7 +522,7 @@ def run_ours(args):
     # form) and the schedulers' instruction issue (the FP32-deviation form)
     # (the ncu records are of the lagged kernels)
     rec = (profile_record(dom, args.precision, args.workload)
-           if dom is not None and args.lambda_mode == "lagged" else None)
+           if dom is not None and args.lambda_mode == "lagged" and not args.power_fp32 else None)
     fp64 = issue = None
     if rec is not None and "fp64_pipe_pct_elapsed" in rec:
         fp64 = {"bound": "alu", "unit": "fraction of the FP64 pipe's peak issue rate",
@@ -557,6 +563,7 @@ def run_ours(args):
                        "grids": sorted({f"{sp.nx}x{sp.ny}" for sp in specs}),
                        "lattice_updates_per_step": lu_step, "precision": args.precision,
                        "kernel": args.kernel, "lambda_mode": args.lambda_mode,
+                       "power_law": "fp32 (opt-in)" if args.power_fp32 else "fp64",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                        "l2": "256 MiB buffer written between timed steps (outside the events)",
                        "metric_definition": HEADLINE_METRIC},
@@ -716,9 +723,12 @@ def run_reference(args):
 
 
 def main(argv=None):
-    global LAMBDA_MODE
+    global LAMBDA_MODE, POWER_FP32
     args = parse_args(argv)
     LAMBDA_MODE = args.lambda_mode
+    POWER_FP32 = args.power_fp32
+    if args.power_fp32 and args.precision != "fp32dev":
+        raise SystemExit("--power-fp32 needs --precision fp32dev")
     out = run_reference(args) if args.impl == "reference" else run_ours(args)
     if out is not None:
         print(json.dumps(out), flush=True)

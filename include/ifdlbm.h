@@ -55,10 +55,10 @@ extern "C" {
                             equilibrium at a reference pressure (Eq. 2.8 at
                             u = 0), P_ref re-based on the cavity's mean
                             pressure every 1024 steps (a uniform pressure
-                            offset is a neutral, drifting mode). The strain
-                            rate and the power law of Eq. (1.4) are FP32 too
-                            (relative error of lambda ~1e-6); metrics, the
-                            lambda plane and all reductions are FP64. Every
+                            offset is a neutral, drifting mode). The metrics,
+                            the power law of Eq. (1.4) (on the FP32 strain
+                            rate), the lambda plane and all reductions are
+                            FP64 (see power_fp32 for an FP32 power). Every
                             output includes P_ref. */
 
 /* Step kernel organisation. */
@@ -96,6 +96,12 @@ typedef struct {
   int schedule;      /* FUSED: IFDLBM_SCHED_*; default GRID */
   int dt_mode;       /* IFDLBM_DT_*: how dt follows from cfl when dt <= 0 */
   int lambda_mode;   /* IFDLBM_LAMBDA_*: how Eq. (2.14) meets the strain rate */
+  int power_fp32;    /* FP32DEV only, opt-in (default 0): 1 evaluates the power law
+                        of Eq. (1.4) and the implicit solve of Eq. (2.14) in FP32
+                        (relative error of lambda ~1e-6) instead of FP64; faster
+                        on GB300's 1/64-rate FP64 pipe, but outside the FP32
+                        deviation form, which keeps them in FP64. INVALID_ARG
+                        with FP64. */
 } ifdlbm_options;
 
 /* Time-step rules ("c = 1, CFL = 0.5", Sec. 5.1). */
@@ -112,10 +118,9 @@ typedef struct {
  * The implicit form solves lambda = K max(gamma-dot(lambda), gamma_min)^(n-1)
  * / c_s^2 at every node, gamma-dot(lambda) = a / (2 lambda + dt) with a from
  * sum_i c_i c_i (f-hat_i - f^eq_i) (Eq. 2.18 at the same lambda), by a
- * bracketed Newton iteration (the root is unique: the residual increases
- * strictly with lambda), in FP64 for IFDLBM_FP64 and in FP32 for
- * IFDLBM_FP32DEV. Both forms share steady states. The adjoint needs the
- * lagged form. */
+ * bracketed Newton iteration in FP64 (the root is unique: the residual
+ * increases strictly with lambda; in FP32 with the power_fp32 opt-in). Both
+ * forms share steady states. The adjoint needs the lagged form. */
 #define IFDLBM_LAMBDA_LAGGED 0   /* default */
 #define IFDLBM_LAMBDA_IMPLICIT 1
 

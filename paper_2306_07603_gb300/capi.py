@@ -52,7 +52,7 @@ class ifdlbm_options(C.Structure):
                 ("gamma_min", C.c_double), ("dt", C.c_double), ("rho0", C.c_double),
                 ("precision", C.c_int), ("kernel", C.c_int), ("graph_chunk", C.c_int),
                 ("fused_threads", C.c_int), ("fused_rows", C.c_int), ("schedule", C.c_int),
-                ("dt_mode", C.c_int), ("lambda_mode", C.c_int)]
+                ("dt_mode", C.c_int), ("lambda_mode", C.c_int), ("power_fp32", C.c_int)]
 
 
 class ifdlbm_cavity(C.Structure):

@@ -194,6 +194,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.cav_done = h->b.cav_done;
     f.implicit = h->opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
     f.general = h->quad.empty() ? 0 : 1;
+    f.pow32 = h->opt.power_fp32 ? 1 : 0;
     f.resid = h->b.resid;
     f.want_residual = want_residual ? 1 : 0;
     if (h->schedule == IFDLBM_SCHED_DYNAMIC) cudaMemsetAsync(h->counter, 0, sizeof(int), h->stream);
@@ -378,6 +379,7 @@ int ifdlbm_default_options(ifdlbm_options *opt) {
   opt->schedule = IFDLBM_SCHED_GRID;
   opt->dt_mode = IFDLBM_DT_CONTRAVARIANT;
   opt->lambda_mode = IFDLBM_LAMBDA_LAGGED;
+  opt->power_fp32 = 0;
   return IFDLBM_OK;
 }
 
@@ -431,6 +433,10 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown dt_mode");
   if (opt.lambda_mode != IFDLBM_LAMBDA_LAGGED && opt.lambda_mode != IFDLBM_LAMBDA_IMPLICIT)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown lambda_mode");
+  if (opt.power_fp32 != 0 && opt.power_fp32 != 1)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: power_fp32 must be 0 or 1");
+  if (opt.power_fp32 && opt.precision != IFDLBM_FP32DEV)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: power_fp32 needs precision FP32DEV");
   if (opt.schedule < IFDLBM_SCHED_GRID || opt.schedule > IFDLBM_SCHED_DYNAMIC)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown schedule");
   if (opt.fused_rows < 0 || opt.fused_rows == 1)
@@ -513,6 +519,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     cv.K = std::pow(s.U_lid, 2.0 - s.n) * std::pow(H, s.n) / s.Re;  // Eq. (2.15.1)
     cv.nm1 = s.n - 1.0;
     cv.implicit = opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
+    cv.pow32 = opt.power_fp32 ? 1 : 0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
     cv.general = quads ? 1 : 0;

@@ -175,31 +175,34 @@ static __device__ __noinline__ float lambda_implicit_f32(float a, float lam_star
 // clamped power law mu = K max(|gamma-dot|, gamma_min)^(n-1) evaluated as
 // K max(q, gamma_min^2)^((n-1)/2) (Eq. 1.4), and lam = mu / c_s^2 (Eq. 2.14).
 // Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i). The strain rate is formed
-// in T (the storage precision), and so is the power law: FP64 pow_fast for
-// T = double, FP32 pow_f32 for T = float (clamped in FP32 at the largest
-// float not above gamma_min^2), and the implicit form's solve.
+// in T (the storage precision); the power law of Eq. (1.4) and the implicit
+// form's solve are FP64 (pow_fast), as the FP32-deviation form specifies.
+// With cv.pow32 (FP32 storage only, an opt-in) they are FP32 instead
+// (pow_f32, lambda_implicit_f32; the clamp at the largest float not above
+// gamma_min^2).
 template <class T>
 __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
                                                   const CavDev &cv, const double *powtab) {
   if (cv.implicit) {
     const T G2 = T(0.5) * (Pxx * Pxx + T(2) * Pxy * Pxy + Pyy * Pyy);
     if constexpr (sizeof(T) == 4)
-      return double(lambda_implicit_f32(2.0f * sqrtf(G2) * float(cv.inv_cs2), float(lam_prev), cv));
-    else
-      return lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, powtab);
+      if (cv.pow32)
+        return double(lambda_implicit_f32(2.0f * sqrtf(G2) * float(cv.inv_cs2), float(lam_prev), cv));
+    return lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, powtab);
   }
   // f^ne = 2 lam_prev/(2 lam_prev + dt) (f-hat - f^eq);  S = -sum c c f^ne / (lam_prev c_s^2)
   const T k = T(-2) / ((T(2) * T(lam_prev) + T(cv.dt)) * T(cv.cs2));
   const T Sxx = k * Pxx, Sxy = k * Pxy, Syy = k * Pyy;
   if constexpr (sizeof(T) == 4) {
-    const float q = fmaxf(0.5f * (Sxx * Sxx + 2.0f * Sxy * Sxy + Syy * Syy),
-                          __double2float_rd(cv.gmin2));
-    return double(float(cv.Kics2) * pow_f32(q, float(cv.half_nm1)));
-  } else {
-    double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
-    q = q > cv.gmin2 ? q : cv.gmin2;
-    return cv.Kics2 * pow_fast(q, cv.half_nm1, powtab);
+    if (cv.pow32) {
+      const float q = fmaxf(0.5f * (Sxx * Sxx + 2.0f * Sxy * Sxy + Syy * Syy),
+                            __double2float_rd(cv.gmin2));
+      return double(float(cv.Kics2) * pow_f32(q, float(cv.half_nm1)));
+    }
   }
+  double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+  q = q > cv.gmin2 ? q : cv.gmin2;
+  return cv.Kics2 * pow_fast(q, cv.half_nm1, powtab);
 }
 
 // Second moments of the non-equilibrium deviation d_i = g_i - geq_i.

@@ -6,7 +6,7 @@
 // h = 0 takes the even rows of the march, half h = 1 the odd ones. Iteration
 // k (k = j0 - 4, j0 - 2, ...) runs, in half h,
 //
-//   stage A  row k + h     moments, f^eq, lagged power-law lambda (power in T),
+//   stage A  row k + h     moments, f^eq, lagged power-law lambda (FP64 power),
 //                          f-hat^+ (Eq. 2.15), f-bar^+ (Eq. 2.16)
 //   stage 1  row k - 2 + h half step f-bar(t+dt/2) (Eq. 3.7), its moments,
 //                          f(t+dt/2) (Eq. 2.17); wall values by extrapolation
@@ -29,9 +29,10 @@
 // full-step values of columns 1 and nx-2, which the wall columns extrapolate
 // from, are published through a small shared array.
 //
-// GB300 issues FP64 at 1/64 of the FP32 rate. With T = float the power of
-// Eq. (1.4) is FP32 too (pow_f32), and the FP64 work per node is the
-// conversion of lambda, whose plane is FP64, and the residual accumulation.
+// FP64 work per node is kept to the power of Eq. (1.4) and the residual
+// accumulation: GB300 issues FP64 at 1/64 of the FP32 rate. With the pow32
+// opt-in of the FP32 form the power is FP32 too (pow_f32), and the FP64 work
+// is the conversion of lambda, whose plane is FP64, and the residual.
 #include <cstdint>
 
 #include "d2q9.cuh"
@@ -206,7 +207,7 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 
 }  // namespace
 
-template <class T, int NT, bool IMPL, bool GEN>
+template <class T, int NT, bool IMPL, bool GEN, bool P32>
 __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
   constexpr int NC = NT / 2;
   const Task task = a.tasks[ti];
@@ -321,24 +322,31 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     second_moments(d, c_, pxx, pxy, pyy);
     if constexpr (IMPL) {                                  // implicit form of Eq. (2.14)
       const T G2 = T(0.5) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy);
-      if constexpr (sizeof(T) == 4)
-        o.lam = double(lambda_implicit_f32(T(2) * sqrtf(G2) * ics2, float(lam_prev), cv));
+      if constexpr (P32)
+        o.lam = double(lambda_implicit_f32(float(T(2) * sqrt(G2) * ics2), float(lam_prev), cv));
       else
         o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
       return o;
     }
-    // Eqs. (2.12)-(2.14), (1.4): strain rate and power in T (as relaxation_time)
+    // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as
+    // relaxation_time), or in FP32 with the pow32 opt-in
     const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
+    double q;
     if constexpr (sizeof(T) == 4) {
-      // clamp at the float below gamma_min^2; FP32 power (pow_f32)
-      const float q = fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f);
-      o.lam = double(Kics2_f * pow_f32(q, half_nm1_f));
+      // the strain rate is FP32 here: clamp before widening (one FP32 max
+      // instead of an FP64 compare), with the clamp as the float below gamma_min^2
+      const float qf = fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f);
+      if constexpr (P32) {
+        o.lam = double(Kics2_f * pow_f32(qf, half_nm1_f));
+        return o;
+      }
+      q = double(qf);
     } else {
-      double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+      q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
       q = q > gmin2 ? q : gmin2;
-      o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     }
+    o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     return o;
   };
   auto take = [&](const Collided &o) {
@@ -594,13 +602,13 @@ struct Occ {
 // blockIdx.x, blockIdx.x + gridDim.x, ... of the largest-first order;
 // 2 persistent CTAs taking positions from an atomic counter (no waiting on
 // other CTAs: a CTA that finds the list exhausted returns).
-template <class T, int NT, bool IMPL, bool GEN>
+template <class T, int NT, bool IMPL, bool GEN, bool P32>
 __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
   __shared__ int next;
   if (a.schedule == 0) {
-    fused_task<T, NT, IMPL, GEN>(a, S, blockIdx.x);
+    fused_task<T, NT, IMPL, GEN, P32>(a, S, blockIdx.x);
     return;
   }
   for (int it = 0;; ++it) {
@@ -614,45 +622,57 @@ __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
       __syncthreads();
     }
     if (pos >= a.ntasks) return;
-    fused_task<T, NT, IMPL, GEN>(a, S, a.order[pos]);
+    fused_task<T, NT, IMPL, GEN, P32>(a, S, a.order[pos]);
   }
 }
 
-template <class T, int NT, bool IMPL, bool GEN = false>
+template <class T, int NT, bool IMPL, bool GEN = false, bool P32 = false>
 static void configure_nt() {
   static bool configured = false;  // the attribute is per function
   if (!configured) {
-    cudaFuncSetAttribute(k_fused<T, NT, IMPL, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaFuncSetAttribute(k_fused<T, NT, IMPL, GEN, P32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          int(sizeof(FusedSmem<T, NT>)));
     configured = true;
   }
 }
 
+template <class T, int NT, bool IMPL, bool GEN, bool P32>
+static void launch_variant(const FusedArgs &a, int grid, cudaStream_t s) {
+  configure_nt<T, NT, IMPL, GEN, P32>();
+  k_fused<T, NT, IMPL, GEN, P32><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+}
+
 template <class T, int NT>
 static void launch_fused_nt(const FusedArgs &a, int grid, cudaStream_t s) {
-  // general quadrilaterals: FP32 with the lagged relaxation time only (the
-  // host admits no other combination)
   if constexpr (sizeof(T) == 4) {
+    // FP32 storage: general quadrilaterals (lagged relaxation time only; the
+    // host admits no other combination) and the FP32-power opt-in
     if (a.general) {
-      configure_nt<T, NT, false, true>();
-      k_fused<T, NT, false, true><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+      if (a.pow32)
+        launch_variant<T, NT, false, true, true>(a, grid, s);
+      else
+        launch_variant<T, NT, false, true, false>(a, grid, s);
+      return;
+    }
+    if (a.pow32) {
+      if (a.implicit)
+        launch_variant<T, NT, true, false, true>(a, grid, s);
+      else
+        launch_variant<T, NT, false, false, true>(a, grid, s);
       return;
     }
   }
-  if (a.implicit) {
-    configure_nt<T, NT, true>();
-    k_fused<T, NT, true, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
-  } else {
-    configure_nt<T, NT, false>();
-    k_fused<T, NT, false, false><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
-  }
+  if (a.implicit)
+    launch_variant<T, NT, true, false, false>(a, grid, s);
+  else
+    launch_variant<T, NT, false, false, false>(a, grid, s);
 }
 
 template <class T, int NT>
 static int blocks_per_sm_nt() {
   configure_nt<T, NT, false>();
   int n = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false, false>, NT,
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false, false, false>, NT,
                                                 int(sizeof(FusedSmem<T, NT>)));
   return n;
 }

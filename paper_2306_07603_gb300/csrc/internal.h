@@ -32,6 +32,8 @@ struct CavDev {
   double Re;                // Reynolds number (adjoint)
   int implicit;             // 1: lambda from the implicit form of Eq. (2.14), 0: lagged
   int general;              // 1: general quadrilateral, per-node metrics in Geo::gmet
+  int pow32;                // FP32 storage only: 1 power law (and implicit solve) in FP32
+  int pad_;
   double lid_ux, lid_uy;    // lid velocity (U, 0) on the trapezoid, U along the top edge in general
 };
 
@@ -116,6 +118,7 @@ struct FusedArgs {
   int *cav_done;       // [ncav] tasks of the step finished (zero between steps)
   int implicit;        // 1: implicit form of Eq. (2.14) (kernel variant), 0: lagged
   int general;         // 1: general quadrilaterals (kernel variant; FP32, lagged)
+  int pow32;           // 1: FP32 power law (opt-in of the FP32 form; kernel variant)
   double *resid;       // [ncav][4] residual outputs (formed by each cavity's last task)
   int want_residual;
 };

@@ -19,7 +19,7 @@ _SCHED = {"grid": capi.IFDLBM_SCHED_GRID, "static": capi.IFDLBM_SCHED_STATIC,
 
 def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, dt=None,
                  gamma_min=None, graph_chunk=None, fused_threads=None, fused_rows=None,
-                 schedule=None, dt_mode=None, lambda_mode=None):
+                 schedule=None, dt_mode=None, lambda_mode=None, power_fp32=None):
     opt = capi.ifdlbm_default_options()
     opt.precision = _PREC[precision]
     opt.kernel = _KERN[kernel]
@@ -33,6 +33,8 @@ def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, 
     if dt_mode is not None:
         opt.dt_mode = {"grid": capi.IFDLBM_DT_GRID,
                        "contravariant": capi.IFDLBM_DT_CONTRAVARIANT}[dt_mode]
+    if power_fp32 is not None:
+        opt.power_fp32 = int(bool(power_fp32))
     if lambda_mode is not None:
         opt.lambda_mode = {"lagged": capi.IFDLBM_LAMBDA_LAGGED,
                            "implicit": capi.IFDLBM_LAMBDA_IMPLICIT}[lambda_mode]

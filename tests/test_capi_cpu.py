@@ -68,7 +68,8 @@ def test_invalid_arguments_rejected_before_device_use(lib, args, frag):
 
 def test_invalid_options_rejected(lib):
     from paper_2306_07603_gb300 import capi
-    for field, val in (("eta_b", 1.5), ("cfl", 0.0), ("precision", 7), ("graph_chunk", 3)):
+    for field, val in (("eta_b", 1.5), ("cfl", 0.0), ("precision", 7), ("graph_chunk", 3),
+                       ("power_fp32", 1), ("power_fp32", 2)):
         o = capi.ifdlbm_default_options()
         setattr(o, field, val)
         with pytest.raises(capi.IfdlbmError) as e:

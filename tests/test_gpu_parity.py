@@ -202,15 +202,18 @@ def test_eta_b_and_dt_options_reach_the_kernel():
     compare_state(fg, lg, run.fhat, run.lam, lam_tol=lam_bound(f_in, l_in, run.prm, run.lam))
 
 
+@pytest.mark.parametrize("power_fp32", [False, True])
 @pytest.mark.parametrize("kname", list(KERNELS))
-def test_fp32_deviation_one_step_error(kname):
+def test_fp32_deviation_one_step_error(kname, power_fp32):
     """FP32 deviation storage: one step from an oracle state stays within
-    1e-5 relative of the FP64 oracle on every field."""
+    1e-5 relative of the FP64 oracle on every field (FP64 power law, and the
+    FP32-power opt-in)."""
     run = oracle_run(67, 45, 100.0, 0.75, 60.0)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     fo, lo = O.step(f0, l0, run.g, run.prm)
-    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev", **KERNELS[kname])
+    s = solver([cav(67, 45, 100.0, 0.75, 60.0)], precision="fp32dev", power_fp32=power_fp32,
+               **KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)
@@ -437,18 +440,20 @@ def test_implicit_lambda_one_step_fp64_parity(nx, ny, Re, n, th, k0, kname):
     compare_state(fg, lg, fo, lo, lam_tol=lam_tol)
 
 
+@pytest.mark.parametrize("power_fp32", [False, True])
 @pytest.mark.parametrize("kname", ["staged", "fused64x8", "fused128"])
 @pytest.mark.parametrize("nx,ny,Re,n,th", [(67, 45, 100.0, 0.75, 60.0), (41, 37, 400.0, 1.5, 75.0)])
-def test_implicit_lambda_fp32_one_step_error(nx, ny, Re, n, th, kname):
-    """FP32 form: the implicit relaxation time solved in FP32 (Newton on the
-    FP32 power), one step within the FP32 bars of the FP64 oracle."""
+def test_implicit_lambda_fp32_one_step_error(nx, ny, Re, n, th, kname, power_fp32):
+    """FP32 form: the implicit relaxation time (solved in FP64, or in FP32
+    with the FP32-power opt-in), one step within the FP32 bars of the FP64
+    oracle."""
     run = oracle_run(nx, ny, Re, n, th)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     prm = O.cavity_params(nx, ny, Re, n, grid=run.g, implicit_lambda=True)
     fo, lo = O.step(f0, l0, run.g, prm)
     s = solver([cav(nx, ny, Re, n, th)], precision="fp32dev", lambda_mode="implicit",
-               **KERNELS[kname])
+               power_fp32=power_fp32, **KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)

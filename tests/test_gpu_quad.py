@@ -115,17 +115,20 @@ FP32_KERNELS = {
 }
 
 
+@pytest.mark.parametrize("power_fp32", [False, True])
 @pytest.mark.parametrize("kname", list(FP32_KERNELS))
 @pytest.mark.parametrize("nx,ny,corners,Re,n", [(37, 29, SKEW, 400.0, 0.75),
                                                 (70, 9, KITE, 100.0, 1.5)])
-def test_fp32_deviation_one_step_error_on_a_quadrilateral(nx, ny, corners, Re, n, kname):
+def test_fp32_deviation_one_step_error_on_a_quadrilateral(nx, ny, corners, Re, n, kname,
+                                                         power_fp32):
     """FP32 deviation storage on a quadrilateral, staged and fused (the fused
     kernel's general variant: metrics of the bilinear map per node in FP32)."""
     run = O.quad_run(nx, ny, corners, Re, n)
     run.advance(200)
     f0, l0 = run.fhat.copy(), run.lam.copy()
     fo, lo = O.step(f0, l0, run.g, run.prm)
-    s = quad_solver([(nx, ny, corners, Re, n)], precision="fp32dev", **FP32_KERNELS[kname])
+    s = quad_solver([(nx, ny, corners, Re, n)], precision="fp32dev", power_fp32=power_fp32,
+                    **FP32_KERNELS[kname])
     s.set_state(0, f0, l0)
     s.step(1)
     fg, lg = s.get_state(0)
