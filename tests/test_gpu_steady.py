@@ -14,7 +14,8 @@ max-norm residual there is ~1e-11). Bars:
   towards its own steady state along the slowest cavity mode (time constant
   ~44k steps at 65^2), so it is compared once that difference has levelled
   off (measured: 7e-6 / 1.6e-5 / 1.8e-5 for u / v / psi at 130k steps,
-  2.5e-6 / 5.3e-6 / 5.9e-6 from 500k steps on).
+  2.4e-6 / 5.1e-6 / 5.4e-6 from 500k steps on; 2.5e-6 / 5.3e-6 / 5.9e-6 with
+  the FP32 power law of the power_fp32 opt-in).
 
 A steady velocity field is an attractor of the step, so rounding differences
 do not grow along the run and the FP64 bar is the per-step bar. The mean of P
