@@ -47,6 +47,8 @@ def test_default_options(lib):
     o = capi.ifdlbm_default_options()
     assert (o.cfl, o.c, o.eta_b, o.rho0) == (0.5, 1.0, 0.5, 1.0)
     assert o.precision == capi.IFDLBM_FP64 and o.graph_chunk == 32
+    # the FP32-deviation form keeps the power law in FP64 unless the opt-in is set
+    assert o.power_fp32 == 0 and o.lambda_mode == capi.IFDLBM_LAMBDA_LAGGED
 
 
 @pytest.mark.parametrize("args,frag", [
