@@ -2,6 +2,7 @@
 
 * free-stream preservation on the skewed theta = 60 deg mesh;
 * steady power-law Poiseuille flow (textbook closed form), n < 1, = 1, > 1;
+* plane Couette flow under a moving lid (the moving-wall branch of the wall rule);
 * Taylor-Green vortex decay rate for n = 1 (exact Navier-Stokes solution);
 * second-order grid convergence of that decay rate;
 * the primary-eddy centre of the paper's Table 2 (slow; loose tolerance).
@@ -77,6 +78,55 @@ def test_power_law_poiseuille_profile_and_convergence(n, tol33):
     assert e17 / e33 > 2.5, (e17, e33)
     assert v33 < 1e-6 * 0.05
     assert gre < 1e-6
+
+
+def _couette(n, ny, U, mu=0.01, nx=4):
+    """Channel periodic in x, bottom wall at rest, top wall (the lid) moving at
+    (U, 0). The steady Navier-Stokes solution is u = U y / H for every power-law
+    index: the shear rate U / H is uniform, so is mu = K (U/H)^(n-1), and the
+    momentum balance reduces to d^2u/dy^2 = 0. K is set so that mu is the given
+    value. The run starts from that profile with f-hat = f^eq and advances until
+    the max-norm velocity residual is below 1e-14; the lid enters only through
+    the moving-wall branch of the non-equilibrium extrapolation (Sec. 4).
+    Returns (max |u - U y/H| / U, max |v| / U)."""
+    H = 1.0
+    K = mu / (U / H) ** (n - 1.0)
+    deta = H / (ny - 1)
+    g = O.periodic_grid(nx, ny, nx * deta, H, periodic_eta=False)
+    z = np.zeros(nx)
+    g.wall_u = dict(bottom=(z, z), top=(np.full(nx, U), z))
+    prm = O.Params(dt=0.5 * deta, K=K, n=n, gamma_min=1e-3 * U / H, eta_b=0.5)
+    exact = U * g.y / H
+    fhat, lam = O.initial_state(g, prm, ux0=exact)
+    run = O.Run(g=g, prm=prm, fhat=fhat, lam=lam)
+    for _ in range(100):
+        run.advance(199)
+        run.advance(1, record=True)
+        if run.history[-1][2] < 1e-14:
+            break
+    assert run.history[-1][2] < 1e-14, run.history[-1]
+    ux, uy, _ = O.macros(run.fhat)
+    return np.abs(ux - exact).max() / U, np.abs(uy).max() / U
+
+
+def test_plane_couette_newtonian_exact():
+    """n = 1: the kinetic scheme holds the linear profile to rounding."""
+    du, dv = _couette(1.0, 17, U=0.05)
+    assert du < 1e-12 and dv < 1e-12, (du, dv)
+
+
+@pytest.mark.parametrize("n", [0.5, 0.75, 1.5])
+def test_plane_couette_power_law(n):
+    """n != 1: the profile is U y / H up to the O(Ma^2) term by which the strain
+    rate of Eqs. (2.12)-(2.13) (from f^ne) departs from the velocity gradient;
+    through mu(gamma-dot) it bends the profile slightly. That term falls as U^2:
+    halving U divides the relative deviation by 4. A wrong lid velocity, a lid
+    rule that drops the wall term, or a non-uniform viscosity from a wrong
+    exponent would leave an O(1) error instead."""
+    d1, v1 = _couette(n, 9, U=0.02)
+    d2, v2 = _couette(n, 9, U=0.01)
+    assert d2 < 2e-9 and v2 < 1e-10, (d2, v2)
+    assert 3.9 < d1 / d2 < 4.1, (d1, d2)
 
 
 def _taylor_green(N, nu=0.002, U0=0.01, t_end=1.0, t_start=0.25, eta_b=0.5):

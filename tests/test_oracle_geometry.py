@@ -193,3 +193,27 @@ def test_global_relative_error_library_norms():
     z = np.zeros_like(ux)
     assert O.global_relative_error(ux, uy, P, z, z, z)[:2] == (1.0, 1.0)
     assert abs(Rinf - np.hypot(ux - u0, uy - v0).max() / np.hypot(ux, uy).max()) < 1e-14
+
+
+@pytest.mark.parametrize("th", [45.0, 60.0, 75.0, 90.0])
+@pytest.mark.parametrize("nx,ny", [(33, 33), (65, 65), (41, 29)])
+def test_contravariant_time_step_closed_form(th, nx, ny):
+    """Default time step (c = 1, CFL = 0.5 of Sec. 5.1 applied to the
+    contravariant speeds of Eq. 3.4). On the L = H = 1 trapezoid,
+    c_xi = (e_x - e_y x_eta) / x_xi with x_xi = 1 + 2 cot(theta) eta >= 1 and
+    |x_eta| = cot(theta) |2 xi - 1| <= cot(theta), so max |c_xi| = 1 + cot(theta),
+    reached by the diagonal directions at the two bottom corners, and
+    c_eta = e_y gives max |c_eta| = 1. Hence
+    dt = CFL min(dxi / (1 + cot(theta)), deta); at 90 deg, CFL min(dxi, deta)."""
+    cot = 0.0 if th == 90.0 else math.cos(math.radians(th)) / math.sin(math.radians(th))
+    g = O.cavity_grid(nx, ny, 1.0, 1.0, th)
+    prm = O.cavity_params(nx, ny, 100.0, 0.75, grid=g)
+    dxi, deta = 1.0 / (nx - 1), 1.0 / (ny - 1)
+    expect = 0.5 * min(dxi / (1.0 + cot), deta)
+    assert prm.dt == pytest.approx(expect, rel=1e-14)
+    # the grid rule of the same paragraph: CFL min(L dxi, H deta) / c
+    prm_g = O.cavity_params(nx, ny, 100.0, 0.75, grid=g, dt_mode="grid")
+    assert prm_g.dt == pytest.approx(0.5 * min(dxi, deta), rel=1e-14)
+    # CFL scales it linearly
+    prm_c = O.cavity_params(nx, ny, 100.0, 0.75, grid=g, cfl=0.25)
+    assert prm_c.dt == pytest.approx(0.5 * expect, rel=1e-14)
