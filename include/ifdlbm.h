@@ -223,10 +223,13 @@ int ifdlbm_create_batch(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_option
                         void *stream, ifdlbm_handle *out);
 
 /* Creates `ncav` cavities on general quadrilaterals (ifdlbm_quad_cavity,
- * host array). The step keeps one FP64 plane per metric and node (xi_x,
- * xi_y, eta_x, eta_y, x_eta, y_eta, J: 56 bytes per node) and runs on the
- * staged kernels: kernel AUTO selects STAGED for both precisions and FUSED
- * is INVALID_ARG. The default time step applies the Courant number to the
+ * host array). The staged kernels keep one FP64 plane per metric and node
+ * (xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J: 56 bytes per node). The fused
+ * kernel has a general-quadrilateral variant for precision FP32DEV with the
+ * lagged relaxation time (it forms each node's metrics from the map's
+ * separable derivatives): there kernel AUTO selects FUSED and FUSED is
+ * accepted; for FP64 or the implicit relaxation time AUTO selects STAGED and
+ * FUSED is INVALID_ARG. The default time step applies the Courant number to the
  * largest contravariant speeds over all nodes (dt_mode CONTRAVARIANT);
  * dt_mode GRID without an explicit dt is INVALID_ARG. Every other call
  * takes the handle as it takes a trapezoid handle, except the adjoint
@@ -370,8 +373,13 @@ int ifdlbm_profile_read(ifdlbm_handle h, int kernel, double *total_ms, int64_t *
  *  stream   cudaStream_t the two kernels are enqueued on; the call does not
  *           synchronise
  * It works on the calling thread's current device. The first call on each
- * device looks up the scratch array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture on that device. Every
+ * device is its set-up: it looks up the scratch array's device address
+ * (cudaGetSymbolAddress) and loads the entry point's two kernels. Under lazy
+ * module loading (the CUDA default) that is when the driver sets up this
+ * module on the device, the 512 KiB array included, so the first call may
+ * take device memory and can fail when none is left. Make that first call at
+ * set-up time, before any stream capture and before the memory budget is
+ * spent; later calls take nothing. Every
  * call shares the one array, and each call writes every partial it reads
  * (nothing carries over between calls); calls that overlap on the GPU (on
  * different streams, or from different threads) race on it and must be

@@ -330,8 +330,37 @@ def ifdlbm_launch_count() -> int:
     return int(load_library().ifdlbm_launch_count())
 
 
+def _device_f64(name, t, need):
+    """Checks that `t` is a contiguous float64 CUDA tensor on the current
+    device with at least `need` elements (the C entry point takes bare device
+    pointers and cannot check any of this itself)."""
+    if isinstance(t, np.ndarray) or not hasattr(t, "is_cuda"):
+        raise TypeError(f"{name}: expected a CUDA tensor (the call takes device memory only)")
+    import torch
+
+    if not t.is_cuda:
+        raise ValueError(f"{name}: tensor is on the host; device memory is required")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name}: expected float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: tensor must be contiguous")
+    if t.numel() < need:
+        raise ValueError(f"{name}: {t.numel()} elements, {need} needed")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name}: tensor is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+
+
 def ifdlbm_residual_fields_static(nx, ny, u1, v1, p1, u0, v0, p0, out, stream=0):
-    """Eq. (2.19) residuals of caller-owned device fields; allocates nothing."""
+    """Eq. (2.19) residuals of caller-owned device fields; allocates nothing.
+
+    u1, v1, p1, u0, v0, p0: float64 CUDA tensors of at least nx*ny elements,
+    contiguous, on the current device; out: the same with at least 3."""
+    nx, ny = int(nx), int(ny)
+    need = nx * ny if nx > 0 and ny > 0 else 0
+    for name, t in (("u1", u1), ("v1", v1), ("p1", p1), ("u0", u0), ("v0", v0), ("p0", p0)):
+        _device_f64(name, t, need)
+    _device_f64("out", out, 3)
     return _check(load_library().ifdlbm_residual_fields_static(
         int(nx), int(ny), _ptr(u1), _ptr(v1), _ptr(p1), _ptr(u0), _ptr(v0), _ptr(p0), _ptr(out),
         C.c_void_p(int(stream))))

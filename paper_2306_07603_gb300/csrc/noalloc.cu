@@ -65,6 +65,15 @@ int scratch_address(double **ptr) {
     if (e != cudaSuccess || !p)
       return ifd::set_global_error(IFDLBM_ERR_CUDA,
                                    std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    // With lazy module loading the module, and so the array, is set up on
+    // first use; load both kernels here too, so that every device resource
+    // this entry point needs is taken in this one set-up call.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_field_partials);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, k_field_reduce);
+    if (e != cudaSuccess)
+      return ifd::set_global_error(IFDLBM_ERR_CUDA,
+                                   std::string("cudaFuncGetAttributes: ") + cudaGetErrorString(e));
     g_addr[dev] = static_cast<double *>(p);
   }
   *ptr = g_addr[dev];
@@ -93,12 +102,13 @@ extern "C" int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, c
   if (rc) return rc;
   const int nblocks = int((n + kThreads - 1) / kThreads);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  (void)cudaGetLastError();  // a launch error left by earlier, unrelated work is not this call's
   k_field_partials<<<nblocks, kThreads, 0, s>>>(n, u1, v1, p1, u0, v0, p0, part);
   k_field_reduce<<<1, kThreads, 0, s>>>(part, nblocks, out);
-  ifd::count_launches(2);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess)
     return ifd::set_global_error(IFDLBM_ERR_CUDA,
                                  std::string("residual_fields_static launch: ") + cudaGetErrorString(e));
+  ifd::count_launches(2);
   return IFDLBM_OK;
 }

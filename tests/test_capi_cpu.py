@@ -133,6 +133,56 @@ def test_quadrilateral_options_rejected(lib, field, val, frag):
     assert frag in str(e.value)
 
 
+def test_quadrilateral_fused_kernel_accepted_for_fp32_lagged(lib):
+    """The header's statement: for general quadrilaterals FUSED is accepted with
+    FP32DEV and the lagged relaxation time (creation then gets past argument
+    checking to the device, which is absent here), and INVALID_ARG with FP64
+    or with the implicit relaxation time."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.solver import quad_cavity
+    q = [quad_cavity(9, 9, SKEW, 100.0, 0.75)]
+    for prec, lmode, ok in ((capi.IFDLBM_FP32DEV, capi.IFDLBM_LAMBDA_LAGGED, True),
+                            (capi.IFDLBM_FP64, capi.IFDLBM_LAMBDA_LAGGED, False),
+                            (capi.IFDLBM_FP32DEV, capi.IFDLBM_LAMBDA_IMPLICIT, False)):
+        o = capi.ifdlbm_default_options()
+        o.kernel, o.precision, o.lambda_mode = capi.IFDLBM_KERNEL_FUSED, prec, lmode
+        if ok and torch.cuda.is_available():
+            continue
+        with pytest.raises(capi.IfdlbmError) as e:
+            capi.ifdlbm_create_quad_batch(q, o)
+        assert e.value.code == (capi.IFDLBM_ERR_CUDA if ok else capi.IFDLBM_ERR_INVALID_ARG), (
+            prec, lmode, str(e.value))
+    text = open(HEADER).read()
+    assert "FUSED is INVALID_ARG." not in text.split("ifdlbm_create_quad_batch")[0][-900:]
+
+
+def test_static_residual_wrapper_rejects_what_the_c_entry_cannot_check(lib):
+    """ifdlbm_residual_fields_static takes bare device pointers; the binding
+    refuses host arrays, host tensors, other dtypes, non-contiguous or short
+    tensors before anything reaches the library."""
+    import numpy as np
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    nx, ny = 8, 4
+    host = np.zeros(nx * ny)
+    with pytest.raises(TypeError):
+        capi.ifdlbm_residual_fields_static(nx, ny, host, host, host, host, host, host, host)
+    t = torch.zeros(nx * ny, dtype=torch.float64)
+    with pytest.raises(ValueError, match="host"):
+        capi.ifdlbm_residual_fields_static(nx, ny, t, t, t, t, t, t, t)
+    if not torch.cuda.is_available():
+        return
+    d = torch.zeros(nx * ny, dtype=torch.float64, device="cuda")
+    for bad, frag in ((d.float(), "float64"), (d[:-1], "needed"), (d.view(ny, nx).t(), "contiguous")):
+        with pytest.raises(ValueError, match=frag):
+            capi.ifdlbm_residual_fields_static(nx, ny, bad, d, d, d, d, d, d)
+    with pytest.raises(ValueError, match="needed"):
+        capi.ifdlbm_residual_fields_static(nx, ny, d, d, d, d, d, d, d[:2])
+
+
 STRUCTS = ["ifdlbm_geometry", "ifdlbm_options", "ifdlbm_cavity", "ifdlbm_quad_cavity",
            "ifdlbm_info_t", "ifdlbm_tuning", "ifdlbm_eddy"]
 
