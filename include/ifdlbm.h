@@ -281,8 +281,10 @@ int ifdlbm_batch_residual(ifdlbm_handle h, double *out);
 
 /* The same read without waiting: enqueues on the handle's stream the copy of
  * the [ncav][4] residuals into HOST out and, if status is not NULL, of the
- * divergence word into HOST *status (bit 0 set: some step produced a
- * non-finite velocity), and returns at once. out and status should be
+ * status word into HOST *status (bit 0 set: some step produced a
+ * non-finite velocity; bit 1 set: a TMA row load of the fused kernel did not
+ * complete within its bounded wait, which synchronising calls report as
+ * IFDLBM_ERR_TIMEOUT), and returns at once. out and status should be
  * page-locked (cudaHostAlloc or equivalent) for the copy to be
  * asynchronous. They are valid once the stream has reached the copy (an
  * event recorded after this call, or any synchronising call), so a caller
@@ -438,7 +440,16 @@ int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
                         double *ref);
 
-/* Self-test of the FP32 power the FP32-deviation form uses for Eq. (1.4):
+/* Self-test of the FP64 power the FP32-deviation form uses for Eq. (1.4)
+ * (FP32 strain rate, FP64 result): for n DEVICE doubles x[k] whose float
+ * roundings xf_k are normal and > 0, writes out[k] = C xf_k^m as the library
+ * evaluates it for cavity `cavity` of the handle (m = (n - 1)/2, C = K/c_s^2,
+ * the cavity's own table) and out[n + k] = C * CUDA's pow(double(xf_k), m).
+ * `out` is a DEVICE array of 2n doubles; on the handle's stream (no sync).
+ * Errors: INVALID_ARG for a bad handle, cavity or pointers. */
+int ifdlbm_selftest_pow_tab(ifdlbm_handle h, int cavity, int n, const double *x, double *out);
+
+/* Self-test of the FP32 power the FP32-power opt-in uses for Eq. (1.4):
  * for n DEVICE doubles x[k] (finite, > 0 after rounding to float) writes
  * out[k] = float(x[k])^float(m) as the library evaluates it, widened to
  * double, on the handle's stream (no sync). */

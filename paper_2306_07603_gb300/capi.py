@@ -126,6 +126,7 @@ _SIGS = {
                                                 C.c_void_p]),
     "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
     "ifdlbm_selftest_pow_f32": (C.c_int, [_H, C.c_int, _P, C.c_double, _P]),
+    "ifdlbm_selftest_pow_tab": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
@@ -391,6 +392,15 @@ def ifdlbm_adjoint_step(h, state_n, adj, dparams):
 def ifdlbm_selftest_pow(h, x, m, fast, ref):
     return _check(load_library().ifdlbm_selftest_pow(h, int(x.numel()), _ptr(x), float(m),
                                                      _ptr(fast), _ptr(ref)), h)
+
+
+def ifdlbm_selftest_pow_tab(h, cavity, x, out):
+    """out[:n] = the FP32 form's C xf^m for cavity `cavity`, out[n:] = C * CUDA pow
+    (x: float64 CUDA tensor of n arguments, out: float64 CUDA tensor of 2n)."""
+    n = int(x.numel())
+    _device_f64("x", x, n)
+    _device_f64("out", out, 2 * n)
+    return _check(load_library().ifdlbm_selftest_pow_tab(h, int(cavity), n, _ptr(x), _ptr(out)), h)
 
 
 def ifdlbm_selftest_pow_f32(h, x, m, out):

@@ -1,15 +1,19 @@
 // Host implementation of the C ABI declared in include/ifdlbm.h.
 #include <algorithm>
 #include <atomic>
+#include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is found at run time)
+
 #include "fastpow.cuh"
 #include "ifdlbm.h"
 #include "internal.h"
+#include "tma.cuh"
 
 using ifd::CavDev;
 
@@ -51,6 +55,7 @@ struct ifdlbm_ctx {
   ifd::Task *tasks = nullptr;
   int *order = nullptr;
   int *counter = nullptr;
+  unsigned char *tmaps = nullptr;  // [2][ncav] TMA tensor maps of g[0], g[1] (fused kernel)
   // adjoint scratch (allocated on the first adjoint call)
   double *adj_g1 = nullptr, *adj_l1 = nullptr, *adj_fhb = nullptr, *adj_fbarb = nullptr,
          *adj_fbb = nullptr, *adj_lamb2 = nullptr, *adj_ppart = nullptr;
@@ -185,11 +190,13 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
     f.schedule = h->schedule;
     f.g_in = h->b.g[parity];
     f.g_out = h->b.g[parity ^ 1];
+    f.tmap_in = h->tmaps + size_t(parity) * h->ncav * ifd::TMAP_BYTES;
     f.lam_in = h->b.lam[parity];
     f.lam_out = h->b.lam[parity ^ 1];
     f.part = h->b.part;
     f.status = h->b.status;
     f.powtab = h->b.powtab;
+    f.powt = h->b.powt;
     f.pref = h->b.pref;
     f.cav_done = h->b.cav_done;
     f.implicit = h->opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
@@ -217,6 +224,7 @@ void enqueue_step(ifdlbm_ctx *h, int parity, bool want_residual) {
   a.part = h->b.part;
   a.status = h->b.status;
   a.powtab = h->b.powtab;
+  a.powt = h->b.powt;
   a.pref = h->b.pref;
   a.want_residual = want_residual ? 1 : 0;
   timed(h, IFDLBM_KPROF_COLLIDE, [&] { ifd::launch_collide<T>(a, h->ntiles, h->stream); });
@@ -263,7 +271,64 @@ int check_status(ifdlbm_ctx *h) {
   cudaError_t e = cudaMemcpyAsync(&st, h->b.status, sizeof st, cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "status read");
-  if (st & 1u) return fail(h, IFDLBM_ERR_DIVERGED, "a step produced a non-finite velocity");
+  if (st & ifd::STATUS_NONFINITE)
+    return fail(h, IFDLBM_ERR_DIVERGED, "a step produced a non-finite velocity");
+  if (st & ifd::STATUS_TMA_TIMEOUT)
+    return fail(h, IFDLBM_ERR_TIMEOUT, "a TMA row load of the fused kernel did not complete");
+  return IFDLBM_OK;
+}
+
+// cuTensorMapEncodeTiled, looked up in the driver at run time (the library
+// links the static runtime, not the driver library).
+using TmapEncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+TmapEncodeFn tmap_encoder() {
+  static const TmapEncodeFn fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return TmapEncodeFn(nullptr);
+    return reinterpret_cast<TmapEncodeFn>(p);
+  }();
+  return fn;
+}
+
+// Tensor maps of the fused kernel's TMA row loads: per buffer g[p] and cavity,
+// the 9 planes of nx x ny elements (row pitch and plane stride of the arena)
+// as a 3-D tensor (x = xi, y = eta, z = population), box 32 x 1 x 9, columns
+// outside the tensor read as zeros. Only this GPU's own memory is mapped.
+int build_tmaps(ifdlbm_ctx *h, size_t tsize) {
+  static_assert(sizeof(CUtensorMap) == ifd::TMAP_BYTES, "tensor map size");
+  const TmapEncodeFn enc = tmap_encoder();
+  if (!enc) return fail(h, IFDLBM_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  std::vector<CUtensorMap> maps(size_t(2) * h->ncav);
+  for (int p = 0; p < 2; ++p)
+    for (int k = 0; k < h->ncav; ++k) {
+      const CavDev &cv = h->cav[k];
+      void *base = static_cast<char *>(h->b.g[p]) + size_t(9 * cv.off) * tsize;
+      const cuuint64_t dims[3] = {cuuint64_t(cv.nx), cuuint64_t(cv.ny), 9};
+      const cuuint64_t strides[2] = {cuuint64_t(cv.pitch) * tsize, cuuint64_t(cv.plane) * tsize};
+      const cuuint32_t box[3] = {32, 1, 9};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      const CUresult r =
+          enc(&maps[size_t(p) * h->ncav + k],
+              tsize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+              base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(h, IFDLBM_ERR_CUDA,
+                    "cuTensorMapEncodeTiled failed (error " + std::to_string(int(r)) + ")");
+    }
+  cudaError_t e = cudaMemcpyAsync(h->tmaps, maps.data(), maps.size() * sizeof(CUtensorMap),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the host vector goes out of scope
+  if (e != cudaSuccess) return cuda_fail(h, e, "tensor map upload");
+  h->h2d_bytes += int64_t(maps.size() * sizeof(CUtensorMap));
   return IFDLBM_OK;
 }
 
@@ -280,15 +345,23 @@ int build_fused_tasks(ifdlbm_ctx *h, int nt, int rows, int sched) {
   for (int k = 0; k < h->ncav; ++k) {
     CavDev &cv = h->cav[k];
     const int hs = rows ? rows : (h->total_plane < (int64_t(8) << 20) ? 32 : 64);
-    const int sx = (cv.nx + W - 1) / W;
+    // strips of a common width, a multiple of 4 columns (W is one too), so
+    // that every strip starts on a 16-byte boundary: the fused kernel's TMA
+    // row loads start at column i0 - 4 (+ 32 per warp)
+    const int sx0 = (cv.nx + W - 1) / W;
+    const int w4 = (((cv.nx + sx0 - 1) / sx0) + 3) / 4 * 4;
+    const int sx = (cv.nx + w4 - 1) / w4;
+    // a last strip of one column (the right wall alone) would not form column
+    // nx - 2, from which the wall column extrapolates: its start moves 4 left
+    const int shift = (sx >= 2 && cv.nx - (sx - 1) * w4 < 2) ? 4 : 0;
     const int sy = std::max(1, std::min((cv.ny + hs - 1) / hs, cv.ny / 2));
     cv.part0 = int(tasks.size());
     for (int b = 0; b < sy; ++b)
       for (int a = 0; a < sx; ++a) {
         ifd::Task t{};
         t.cav = k;
-        t.i0 = int(int64_t(a) * cv.nx / sx);
-        t.i1 = int(int64_t(a + 1) * cv.nx / sx);
+        t.i0 = a * w4 - (a == sx - 1 ? shift : 0);
+        t.i1 = a == sx - 1 ? cv.nx : (a + 1) * w4 - (a == sx - 2 ? shift : 0);
         t.j0 = int(int64_t(b) * cv.ny / sy);
         t.j1 = int(int64_t(b + 1) * cv.ny / sy);
         tasks.push_back(t);
@@ -348,6 +421,18 @@ void ifd::fill_pow_tables(double *tab) {
     tab[256 + j] = double(-log2l((long double)r));
     tab[512 + j] = double(exp2l((long double)j / 256.0L));
   }
+}
+// Table of pow_tab for exponent m and factor C, in extended precision:
+// [2j] = c_j^m, [2j + 1] = 1/c_j with c_j = 1 + (j + 1/2)/256 (exact), and
+// [512 + e] = C 2^(m (e - 127)), each rounded once to double.
+void ifd::fill_cavity_pow_table(double *tab, double m, double C) {
+  const long double ml = m, Cl = C;
+  for (int j = 0; j < 256; ++j) {
+    const long double c = 1.0L + (j + 0.5L) / 256.0L;
+    tab[2 * j] = double(powl(c, ml));
+    tab[2 * j + 1] = double(1.0L / c);
+  }
+  for (int e = 0; e < 256; ++e) tab[512 + e] = double(Cl * exp2l(ml * (e - 127)));
 }
 void ifd::count_launches(int64_t n) { g_launches += n; }
 
@@ -587,6 +672,16 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     cv.Re = s.Re;
     cv.half_nm1 = 0.5 * cv.nm1;
     cv.Kics2 = cv.K / cv.cs2;
+    {  // pow_tab: binomial coefficients of (1 + t)^m, m = (n - 1)/2, and the FP32 clamp
+      const double m = cv.half_nm1;
+      cv.pb2 = m * (m - 1.0) / 2.0;
+      cv.pb3 = float(cv.pb2 * (m - 2.0) / 3.0);
+      cv.pb4 = float(cv.pb2 * (m - 2.0) * (m - 3.0) / 12.0);
+      cv.pb5 = float(cv.pb2 * (m - 2.0) * (m - 3.0) * (m - 4.0) / 60.0);
+      float g = float(cv.gmin2);
+      if (double(g) > cv.gmin2) g = std::nextafter(g, 0.0f);
+      cv.gmin2_f = std::max(g, FLT_MIN);
+    }
     h->max_n2 = std::max<int64_t>(h->max_n2, int64_t(s.nx) * s.ny);
     // 1-D metric arrays of Eq. (3.8.2)
     xix.resize(goff), xeH.resize(goff), xxi.resize(goff), xeta.resize(goff);
@@ -643,7 +738,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   bool ok = true;
   for (int p = 0; p < 2; ++p) {
     ok &= (h->b.g[p] = A(9 * off * tsize)) != nullptr;
-    ok &= (h->b.lam[p] = (double *)A(off * sizeof(double))) != nullptr;
+    ok &= (h->b.lam[p] = A(off * tsize)) != nullptr;
   }
   if (!fused) {  // scratch planes of the staged kernels
     ok &= (h->b.fb = A(9 * off * tsize)) != nullptr;
@@ -654,6 +749,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     ok &= (h->tasks = (ifd::Task *)A(size_t(h->task_cap) * sizeof(ifd::Task))) != nullptr;
     ok &= (h->order = (int *)A(size_t(h->task_cap) * sizeof(int))) != nullptr;
     ok &= (h->counter = (int *)A(sizeof(int))) != nullptr;
+    ok &= (h->tmaps = (unsigned char *)A(size_t(2) * ncav * ifd::TMAP_BYTES)) != nullptr;
   }
   const int nslots = fused ? h->task_cap : h->ntiles;
   ok &= (h->b.part = (double *)A(size_t(nslots) * ifd::NPART * sizeof(double))) != nullptr;
@@ -667,6 +763,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   ok &= geof != nullptr;
   ok &= (h->stage = (double *)A(size_t(10 * h->max_n2) * sizeof(double))) != nullptr;
   ok &= (h->b.powtab = (double *)A(ifd::POW_TABLE_SIZE * sizeof(double))) != nullptr;
+  ok &= (h->b.powt = (double *)A(size_t(ncav) * ifd::POWT_SIZE * sizeof(double))) != nullptr;
   ok &= (h->b.pref = (double *)A(size_t(ncav) * sizeof(double))) != nullptr;
   ok &= (h->b.cav_done = (int *)A(size_t(ncav) * sizeof(int))) != nullptr;
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
@@ -728,6 +825,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
                          geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
                          ifd::POW_TABLE_SIZE * sizeof(double) + qsep_h.size() * sizeof(float) +
+                         size_t(ncav) * ifd::POWT_SIZE * sizeof(double) +
                          (quads ? size_t(8 * ncav) * sizeof(double) : 0));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
                       cudaMemcpyHostToDevice, s);
@@ -764,12 +862,20 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->b.powtab, powtab_h.data(), powtab_h.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s);
+  std::vector<double> powt_h(size_t(ncav) * ifd::POWT_SIZE);
+  for (int k = 0; k < ncav; ++k)
+    ifd::fill_cavity_pow_table(powt_h.data() + size_t(k) * ifd::POWT_SIZE, h->cav[k].half_nm1,
+                               h->cav[k].Kics2);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->b.powt, powt_h.data(), powt_h.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
   // every buffer starts zeroed so that no read can ever see uninitialised memory
   for (void *ptr : {h->b.fb, h->b.fp, h->b.fh, h->b.g[1]})
     if (ptr && e == cudaSuccess) e = cudaMemsetAsync(ptr, 0, 9 * off * tsize, s);
   if (h->b.m0 && e == cudaSuccess) e = cudaMemsetAsync(h->b.m0, 0, 3 * off * sizeof(double), s);
   if (fused && e == cudaSuccess) {
-    int rc = build_fused_tasks(h, h->fused_nt, opt.fused_rows, opt.schedule);
+    int rc = build_tmaps(h, tsize);
+    if (!rc) rc = build_fused_tasks(h, h->fused_nt, opt.fused_rows, opt.schedule);
     if (rc) {
       std::string msg = h->err;
       release_all(h);
@@ -778,7 +884,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     }
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->b.lam[1], 0, off * tsize, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.resid, 0, size_t(ncav) * 4 * sizeof(double), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.status, 0, sizeof(unsigned), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->b.pref, 0, size_t(ncav) * sizeof(double), s);
@@ -1069,8 +1175,7 @@ int ifdlbm_set_state(ifdlbm_handle h, int cavity, const double *fhat, const doub
 int64_t ifdlbm_state_bytes(ifdlbm_handle h) {
   if (!h) return -1;
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
-  return int64_t(9 * h->total_plane * tsize + h->total_plane * sizeof(double) +
-                 h->ncav * sizeof(double));
+  return int64_t(9 * h->total_plane * tsize + h->total_plane * tsize + h->ncav * sizeof(double));
 }
 
 int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst) {
@@ -1078,7 +1183,7 @@ int ifdlbm_save_state_dev(ifdlbm_handle h, void *dst) {
   cudaSetDevice(h->device);
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
   const size_t gb = 9 * h->total_plane * tsize;
-  const size_t lb = h->total_plane * sizeof(double);
+  const size_t lb = h->total_plane * tsize;
   cudaError_t e = cudaMemcpyAsync(dst, h->b.g[h->cur], gb, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((char *)dst + gb, h->b.lam[h->cur], lb, cudaMemcpyDeviceToDevice,
@@ -1095,7 +1200,7 @@ int ifdlbm_load_state_dev(ifdlbm_handle h, const void *src) {
   cudaSetDevice(h->device);
   const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
   const size_t gb = 9 * h->total_plane * tsize;
-  const size_t lb = h->total_plane * sizeof(double);
+  const size_t lb = h->total_plane * tsize;
   cudaError_t e = cudaMemcpyAsync(h->b.g[h->cur], src, gb, cudaMemcpyDeviceToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->b.lam[h->cur], (const char *)src + gb, lb, cudaMemcpyDeviceToDevice,
@@ -1338,6 +1443,21 @@ int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, doubl
   g_launches += 1;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(h, e, "selftest_pow");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_selftest_pow_tab(ifdlbm_handle h, int cavity, int n, const double *x, double *out) {
+  if (!cavity_ok(h, cavity) || n < 0 || (n > 0 && (!x || !out)))
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "selftest_pow_tab: bad arguments");
+  if (n == 0) return IFDLBM_OK;
+  cudaSetDevice(h->device);
+  const CavDev &cv = h->cav[cavity];
+  ifd::launch_pow_tab_selftest(n, x, cv.half_nm1, cv.Kics2,
+                               h->b.powt + size_t(cavity) * ifd::POWT_SIZE, cv.pb2, cv.pb3,
+                               cv.pb4, cv.pb5, out, h->stream);
+  g_launches += 1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "selftest_pow_tab");
   return IFDLBM_OK;
 }
 

@@ -176,13 +176,15 @@ static __device__ __noinline__ float lambda_implicit_f32(float a, float lam_star
 // K max(q, gamma_min^2)^((n-1)/2) (Eq. 1.4), and lam = mu / c_s^2 (Eq. 2.14).
 // Pxx, Pxy, Pyy are sum_i c_ia c_ib (g_i - geq_i). The strain rate is formed
 // in T (the storage precision); the power law of Eq. (1.4) and the implicit
-// form's solve are FP64 (pow_fast), as the FP32-deviation form specifies.
-// With cv.pow32 (FP32 storage only, an opt-in) they are FP32 instead
-// (pow_f32, lambda_implicit_f32; the clamp at the largest float not above
-// gamma_min^2).
+// form's solve are FP64, as the FP32-deviation form specifies: pow_fast for
+// an FP64 strain rate, pow_tab (FP64 result, error within 6e-16) for the FP32
+// one, clamped at cv.gmin2_f. With cv.pow32 (FP32 storage only, an opt-in)
+// they are FP32 instead (pow_f32, lambda_implicit_f32; the clamp at the
+// largest float not above gamma_min^2). powt: the cavity's pow_tab table.
 template <class T>
 __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double lam_prev,
-                                                  const CavDev &cv, const double *powtab) {
+                                                  const CavDev &cv, const double *powtab,
+                                                  const double *powt) {
   if (cv.implicit) {
     const T G2 = T(0.5) * (Pxx * Pxx + T(2) * Pxy * Pxy + Pyy * Pyy);
     if constexpr (sizeof(T) == 4)
@@ -199,6 +201,8 @@ __device__ __forceinline__ double relaxation_time(T Pxx, T Pxy, T Pyy, double la
                             __double2float_rd(cv.gmin2));
       return double(float(cv.Kics2) * pow_f32(q, float(cv.half_nm1)));
     }
+    const float q = fmaxf(0.5f * (Sxx * Sxx + 2.0f * Sxy * Sxy + Syy * Syy), cv.gmin2_f);
+    return pow_tab(q, powt, cv.half_nm1, cv.pb2, cv.pb3, cv.pb4, cv.pb5);
   }
   double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
   q = q > cv.gmin2 ? q : cv.gmin2;

@@ -56,6 +56,48 @@ __device__ __forceinline__ double pow_fast(double x, double m, const double *__r
   return __hiloint2double(__double2hiint(res) + ((N >> 8) << 20), __double2loint(res));
 }
 
+// C x^m in FP64 for an FP32 argument x (the strain rate of the FP32-deviation
+// form is formed in FP32): a table-driven binomial evaluation with 7 FP64
+// instructions. With x = 2^(e-127) f, f in [1, 2) its fraction, j the leading 8
+// bits of the fraction and c_j = 1 + (j + 1/2)/256 the centre of that interval,
+//
+//   C x^m = [C 2^(m (e - 127))] [c_j^m] (1 + t)^m,   t = f / c_j - 1, |t| <= 2^-9,
+//
+// the first two factors come from per-cavity FP64 tables built on the host in
+// extended precision, and (1 + t)^m = 1 + b1 t + b2 t^2 + ... + b5 t^5 is the
+// binomial series (b_k = m (m-1) ... (m-k+1) / k!; the next term is below
+// 2^-54 |b6| for |t| <= 2^-9). t is formed in FP64 from the exact fraction as
+// f (1/c_j) - 1 (absolute error <= 1.2e-16); the terms from t^3 on, whose sum
+// is below 1e-9, take their coefficient c3 = b3 + b4 t + b5 t^2 in FP32 (its
+// error reaches the sum as t^3 dc3 < 1e-16). Relative error: table roundings
+// (2 x 2^-53), the products and the final fma (3 x 2^-53) and the series
+// (< 2e-16): within 6e-16 for every normal x > 0, independent of m log2 x
+// (checked against CUDA's pow by the self-test entry point). The argument
+// must be a normal float (the callers clamp it at or above FLT_MIN).
+//
+// Per-cavity table (POWT_SIZE doubles): [2j] = c_j^m, [2j + 1] = 1/c_j
+// (j = 0..255); [512 + e] = C 2^(m (e - 127)) (e = 0..255).
+constexpr int POWT_SIZE = 768;
+
+__device__ __forceinline__ double pow_tab(float x, const double *__restrict__ tab, double b1,
+                                          double b2, float b3, float b4, float b5) {
+  const unsigned bits = __float_as_uint(x);
+  const unsigned e = bits >> 23;                 // biased exponent (x > 0)
+  const unsigned j = (bits >> 15) & 255u;        // leading 8 bits of the fraction
+  const unsigned frac = bits & 0x7FFFFFu;
+  // the fraction 1.frac exactly, as a double (integer moves, no conversion)
+  const double f = __hiloint2double(int(0x3FF00000u | (frac >> 3)), int(frac << 29));
+  const double2 dr = __ldg(reinterpret_cast<const double2 *>(tab) + j);
+  const double t = fma(f, dr.y, -1.0);           // f / c_j - 1
+  // t to ~1e-7 for the tail: f - c_j is exact in FP32 (both in [1, 2), 2^-9 apart at most)
+  const float cj = __uint_as_float(0x3F804000u | (j << 15));
+  const float tf = __fdividef(__uint_as_float(0x3F800000u | frac) - cj, cj);
+  const float c3 = fmaf(tf, fmaf(tf, b5, b4), b3);
+  const double w = fma(t, fma(t, double(c3), b2), b1);
+  const double P = __ldg(tab + 512 + e) * dr.x;  // C 2^(m (e - 127)) c_j^m
+  return fma(P, t * w, P);
+}
+
 // x^m in FP32 for the FP32-deviation form: 2^(m log2 x) with CUDA's log2f
 // and exp2f (1 and 2 ulp by the CUDA math documentation). For normal x > 0
 // its relative error is about ln2 2^-24 (2 |m log2 x| + |m log2 x|) from the

@@ -17,10 +17,13 @@
 // Shared memory per column pair: six-row rings of f-bar^+ and f(t+dt/2)
 // (slot = row mod 6), read across columns (xi stencils) and across the two
 // halves (eta stencils); and, per thread, five slots that hold the state of a
-// row from its cp.async prefetch (two iterations ahead) until stage A, and
-// then, in place, its f-hat^+ until the full step two iterations later. That
-// is ~410 B per thread in FP32, so that 16 warps fit on an SM. Four barriers
-// per iteration (two per row) order the stages across the halves.
+// row from its prefetch (two iterations ahead) until stage A, and then, in
+// place, its f-hat^+ until the full step two iterations later. The prefetch is
+// one TMA copy per warp (tma.cuh): a 3-D tiled bulk copy of the warp's 32
+// columns x 9 planes of the row into the warp's slot, completed on that slot's
+// mbarrier, so that no thread issues per-population loads. That is ~410 B per
+// thread in FP32, so that 16 warps fit on an SM. Four barriers per iteration
+// (two per row) order the stages across the halves.
 //
 // Wall nodes follow the rule of the staged kernels: a side-wall node takes
 // its inner neighbour on the same row, a bottom/lid node the node
@@ -38,6 +41,7 @@
 #include "d2q9.cuh"
 #include "internal.h"
 #include "reduce.cuh"
+#include "tma.cuh"
 
 namespace ifd {
 
@@ -49,28 +53,23 @@ constexpr int RING = 6;   // rows of the f-bar^+ and f(t+dt/2) rings
 
 template <class T, int NT>
 struct FusedSmem {
-  static constexpr int NC = NT / 2;
-  T sf[PF][9][NT];        // per thread: g(t) of its rows, then f-hat^+ in place
+  static constexpr int NC = NT / 2, NW = NT / 32;
+  // per warp and slot, the TMA box of its 32 columns x 9 planes: g(t) of the
+  // warp's row, then f-hat^+ in place (each box a multiple of 128 bytes)
+  T sf[PF][NW][9][32];
   T fb[RING][9][NC];      // f-bar^+
   T fh[RING][9][NC];      // f(t + dt/2)
   T edge[2][3][NC];       // u, v, P(t) of rows 0 and ny-1 (wall-row residuals)
   T gw[2][2][9];          // f-hat(t+dt) of columns 1 and nx-2, per half
+  uint64_t bar[PF][NW];   // mbarriers of the TMA row loads
 };
+// dynamic shared memory: the struct plus the slack of aligning it to 128 bytes
+template <class T, int NT>
+constexpr int fused_smem_size() {
+  return int(sizeof(FusedSmem<T, NT>)) + 128;
+}
 
 __device__ __forceinline__ int slot6(int r) { return (r + 12) % RING; }
-
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
-  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-  if (bytes == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
-  else
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
 
 // Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side known
 // at compile time (eta direction: the side is the sign of e_iy, since
@@ -208,8 +207,10 @@ __device__ __forceinline__ void leaf_add(Leaf<T> &l, Partial &p, T u1, T v1, T P
 }  // namespace
 
 template <class T, int NT, bool IMPL, bool GEN, bool P32>
-__device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti) {
+__device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> &S, int ti,
+                                           unsigned &phase) {
   constexpr int NC = NT / 2;
+  constexpr int SLOT = FusedSmem<T, NT>::NW * 9 * 32;  // elements of one slot (all warps)
   const Task task = a.tasks[ti];
   const CavDev &cv = a.cav[task.cav];
   const int i0 = task.i0, i1 = task.i1, j0 = task.j0, j1 = task.j1;
@@ -249,10 +250,9 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const bool clo = c == 1, chi = c == nx - 2;
 
   const int64_t b9 = 9 * cv.off;
-  const T *gin = (const T *)a.g_in + b9;
   T *gout = (T *)a.g_out + b9;
-  const double *lam_in = a.lam_in + cv.off;
-  double *lam_out = a.lam_out + cv.off;
+  const T *lam_in = (const T *)a.lam_in + cv.off;   // relaxation time, storage type T
+  T *lam_out = (T *)a.lam_out + cv.off;
 
   const T c_ = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
   const T dt = T(cv.dt), hdt = T(0.5 * cv.dt);
@@ -278,41 +278,60 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const int olo = max(1, j0), ohi = min(ny - 2, j1 - 1);      // rows of the full step
   const int nit = (j1 + 3 - kb) / 2 + 1;                      // k = kb + 2 it, it < nit
   auto row_of = [&](int it) { return kb + 2 * it + h; };      // this thread's stage-A row
+  // Row prefetch: lane 0 of each warp copies the warp's 32 columns (from
+  // column i0 - 4 + 32 (l / 32), a multiple of 4 since strips start at
+  // multiples of 4) x 9 planes of row r into the warp's box of slot it % PF,
+  // by TMA; columns outside the cavity arrive as zeros. The warp waits on the
+  // slot's mbarrier before it reads the box (wait_row).
+  const int wid = t >> 5, lane = t & 31;
+  T *const sfme = &S.sf[0][wid][0][lane];               // this thread's column of slot 0
+  const int tx = i0 - 4 + (l & ~31);
+  const void *tmap = static_cast<const char *>(a.tmap_in) + size_t(task.cav) * TMAP_BYTES;
   auto prefetch = [&](int it) {
+    const int r = row_of(it);
+    if (lane == 0 && r >= rlo && r <= rhi && (tx & 3) == 0)
+      tma_load_box3(&S.sf[it % PF][wid][0][0], tmap, tx, r, &S.bar[it % PF][wid],
+                    uint32_t(9 * 32 * sizeof(T)));
+  };
+  auto wait_row = [&](int it) {
     const int r = row_of(it);
     if (r >= rlo && r <= rhi) {
       const int s = it % PF;
-      const int64_t node = int64_t(r) * pitch + cc;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) cp_async(&S.sf[s][q][t], gin + q * plane + node, sizeof(T));
+      const bool ok = (tx & 3) == 0 && mbar_wait(&S.bar[s][wid], (phase >> s) & 1u);
+      if (!ok && lane == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
+      if ((tx & 3) == 0) phase ^= 1u << s;
     }
-    cp_commit();
   };
   // lambda_prev of a row Step (2) works on, loaded one iteration ahead
   auto lam_load = [&](int r) {
-    return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * pitch + cc] : 0.0;
+    return (r >= rlo && r <= rhi) ? lam_in[int64_t(r) * pitch + cc] : T(0);
   };
   // per-cavity constants of the relaxation time
   const double gmin2 = cv.gmin2, half_nm1 = cv.half_nm1, Kics2 = cv.Kics2;
-  // largest float not above gamma_min^2 (so that every clamped q is >= it)
-  const float gmin2_f = __double2float_rd(gmin2);
+  // the FP32 strain rate's clamp: the largest float not above gamma_min^2 (so
+  // that every clamped q is >= it), and not below FLT_MIN
+  const float gmin2_f = cv.gmin2_f;
   const float half_nm1_f = float(half_nm1), Kics2_f = float(Kics2);
+  // pow_tab of the FP32 form: the cavity's table and binomial coefficients
+  const double *powt = a.powt + int64_t(task.cav) * POWT_SIZE;
+  const double pb2 = cv.pb2;
+  const float pb3 = cv.pb3, pb4 = cv.pb4, pb5 = cv.pb5;
   const T wy_in = T(cv.deta), wy_edge = T(0.5 * cv.deta);
   // Step (2) for this thread's row of iteration `it`: moments, f^eq and
   // lambda(t). The row of iteration it + 1 is formed during the full step of
   // iteration it, so that the power overlaps the stencil work.
   T nux = 0, nuy = 0, nP = 0, ngeq[9];
-  double nlam = 0.0;
+  T nlam = T(0);
   struct Collided {
     T ux, uy, P, geq[9];
-    double lam;
+    T lam;
   };
-  auto collide = [&](int it, double lam_prev) {
+  auto collide = [&](int it, T lam_prev) {
     Collided o;
     const int s = it % PF;
     T g[9];
 #pragma unroll
-    for (int q = 0; q < 9; ++q) g[q] = S.sf[s][q][t];
+    for (int q = 0; q < 9; ++q) g[q] = sfme[s * SLOT + q * 32];
     moments(g, c_, cs2, o.ux, o.uy, o.P);                 // Eqs. (2.10)-(2.11)
     equilibrium(o.P, o.ux, o.uy, c_, ics2, o.geq);        // Eq. (2.8)
     T d[9];
@@ -323,30 +342,29 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     if constexpr (IMPL) {                                  // implicit form of Eq. (2.14)
       const T G2 = T(0.5) * (pxx * pxx + T(2) * pxy * pxy + pyy * pyy);
       if constexpr (P32)
-        o.lam = double(lambda_implicit_f32(float(T(2) * sqrt(G2) * ics2), float(lam_prev), cv));
+        o.lam = T(lambda_implicit_f32(float(T(2) * sqrt(G2) * ics2), float(lam_prev), cv));
       else
-        o.lam = lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, lam_prev, cv, a.powtab);
+        o.lam = T(lambda_implicit(2.0 * sqrt(double(G2)) * cv.inv_cs2, double(lam_prev), cv,
+                                  a.powtab));
       return o;
     }
     // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as
     // relaxation_time), or in FP32 with the pow32 opt-in
-    const T k = T(-2) / ((T(2) * T(lam_prev) + dt) * cs2);
+    const T k = T(-2) / ((T(2) * lam_prev + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
-    double q;
     if constexpr (sizeof(T) == 4) {
-      // the strain rate is FP32 here: clamp before widening (one FP32 max
-      // instead of an FP64 compare), with the clamp as the float below gamma_min^2
+      // the strain rate is FP32 here: clamped in FP32, then C q^m in FP64 by
+      // pow_tab (7 FP64 instructions) and rounded to the FP32 plane
       const float qf = fmaxf(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy), gmin2_f);
-      if constexpr (P32) {
-        o.lam = double(Kics2_f * pow_f32(qf, half_nm1_f));
-        return o;
-      }
-      q = double(qf);
+      if constexpr (P32)
+        o.lam = Kics2_f * pow_f32(qf, half_nm1_f);
+      else
+        o.lam = float(pow_tab(qf, powt, half_nm1, pb2, pb3, pb4, pb5));
     } else {
-      q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
+      double q = double(T(0.5) * (Sxx * Sxx + T(2) * Sxy * Sxy + Syy * Syy));
       q = q > gmin2 ? q : gmin2;
+      o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     }
-    o.lam = Kics2 * pow_fast(q, half_nm1, a.powtab);
     return o;
   };
   auto take = [&](const Collided &o) {
@@ -359,11 +377,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   };
   auto in_a = [&](int r) { return r >= rlo && r <= rhi; };
 
+  if (lane == 0) tmap_acquire(tmap);
   prefetch(0);
   prefetch(1);
-  cp_wait<1>();
+  wait_row(0);
   if (in_a(row_of(0))) take(collide(0, lam_load(row_of(0))));
-  double lp_next = lam_load(row_of(1));  // lambda_prev of the next row
+  T lp_next = lam_load(row_of(1));       // lambda_prev of the next row
   T Lprev = T(0);                        // lambda(t) of this thread's previous row
   // metrics of this iteration's half-step and full-step rows, loaded one
   // iteration ahead (rows clamped into the cavity; unused outside it)
@@ -384,16 +403,16 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     if (in_a(ar)) {
       const int s = it % PF, sb = slot6(ar);
       if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * pitch + c] = nlam;
-      const T L = T(nlam);
+      const T L = nlam;
       Lcur = L;
       const T i2 = T(1) / (T(2) * L + dt);
       const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
       const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt) = bb
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
-        const T gq = S.sf[s][q][t];
+        const T gq = sfme[s * SLOT + q * 32];
         S.fb[sb][q][l] = toward(gq, ngeq[q], bb);
-        S.sf[s][q][t] = toward(gq, ngeq[q], bp);          // f-hat^+ in place of g
+        sfme[s * SLOT + q * 32] = toward(gq, ngeq[q], bp);  // f-hat^+ in place of g
       }
       if (ar == 0 || ar == ny - 1) {
         const int e = ar == 0 ? 0 : 1;
@@ -470,26 +489,26 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     const int o = k - 4 + h;
     const bool do2 = o >= olo && o <= ohi;
     const int sp = (it + PF - 2) % PF;               // f-hat^+ of row o (iteration it - 2)
-    cp_wait<1>();                                    // this thread's row of iteration it + 1
+    wait_row(it + 1);                                // this warp's row of iteration it + 1
     T gnv[9];
     if (do2 && inner_c && l >= 4 && l < NC - 4) {
       const int so = slot6(o);
       const bool lo = o == 1, hi = o == ny - 2;
-      gnv[0] = S.sf[sp][0][t];
+      gnv[0] = sfme[sp * SLOT];
       {
         const T *cols[5] = {&S.fh[slot6(o - 2)][0][l], &S.fh[slot6(o - 1)][0][l], &S.fh[so][0][l],
                             &S.fh[slot6(o + 1)][0][l], &S.fh[slot6(o + 2)][0][l]};
         if constexpr (GEN) {
           const T X = row_xxi(o), Y = row_yxi(o);
           const T iJ = c_ / (X * gye - gxe * Y);         // c / J of node (c, o)
-          AdvectAllGen<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
+          AdvectAllGen<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
                                           iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, dt,
-                                          &S.sf[sp][0][t], gnv);  // Eq. (3.6)
+                                          sfme + sp * SLOT, gnv);  // Eq. (3.6)
         } else {
           const T A = A2;                                // c xi_x of row o
           const T B = A * xeH;
-          AdvectAll<T, 1, NC, NT>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
-                                       eta_b, i2dxi, i2deta, dt, &S.sf[sp][0][t], gnv);  // Eq. (3.6)
+          AdvectAll<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
+                                       eta_b, i2dxi, i2deta, dt, sfme + sp * SLOT, gnv);  // Eq. (3.6)
         }
       }
       if (clo || chi) {                                // values the wall columns extrapolate
@@ -522,7 +541,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         moments(gnv, c_, cs2, ux, uy, P);
         T fpo[9];
 #pragma unroll
-        for (int q = 0; q < 9; ++q) fpo[q] = S.sf[sp][q][t];
+        for (int q = 0; q < 9; ++q) fpo[q] = sfme[sp * SLOT + q * 32];
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
         T Jo;
         if constexpr (GEN)
@@ -565,8 +584,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         }
       }
     }
+    // this iteration's reads and writes of the warp's boxes are ordered before
+    // the TMA copies that refill them after the next barrier
+    fence_proxy_async_smem();
   }
-  cp_wait<0>();
   if (a.want_residual) {
     leaf_flush(leaf, p);
     p.du2max = double(leaf.du2max);
@@ -605,10 +626,18 @@ struct Occ {
 template <class T, int NT, bool IMPL, bool GEN, bool P32>
 __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  FusedSmem<T, NT> &S = *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw);
+  // the TMA boxes want 128-byte aligned shared memory: align the struct
+  const uint32_t s0 = smem_addr(smem_raw);
+  FusedSmem<T, NT> &S =
+      *reinterpret_cast<FusedSmem<T, NT> *>(smem_raw + (((s0 + 127u) & ~127u) - s0));
   __shared__ int next;
+  constexpr int NW = FusedSmem<T, NT>::NW;
+  if (threadIdx.x < PF * NW) mbar_init(&S.bar[0][0] + threadIdx.x, 1);
+  mbar_init_fence();
+  __syncthreads();
+  unsigned phase = 0;  // bit s: parity of the next completion of slot s's barrier (this warp)
   if (a.schedule == 0) {
-    fused_task<T, NT, IMPL, GEN, P32>(a, S, blockIdx.x);
+    fused_task<T, NT, IMPL, GEN, P32>(a, S, blockIdx.x, phase);
     return;
   }
   for (int it = 0;; ++it) {
@@ -622,7 +651,7 @@ __global__ void __launch_bounds__(NT, Occ<T, NT>::blocks) k_fused(FusedArgs a) {
       __syncthreads();
     }
     if (pos >= a.ntasks) return;
-    fused_task<T, NT, IMPL, GEN, P32>(a, S, a.order[pos]);
+    fused_task<T, NT, IMPL, GEN, P32>(a, S, a.order[pos], phase);
   }
 }
 
@@ -631,7 +660,7 @@ static void configure_nt() {
   static bool configured = false;  // the attribute is per function
   if (!configured) {
     cudaFuncSetAttribute(k_fused<T, NT, IMPL, GEN, P32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(sizeof(FusedSmem<T, NT>)));
+                         fused_smem_size<T, NT>());
     configured = true;
   }
 }
@@ -639,7 +668,7 @@ static void configure_nt() {
 template <class T, int NT, bool IMPL, bool GEN, bool P32>
 static void launch_variant(const FusedArgs &a, int grid, cudaStream_t s) {
   configure_nt<T, NT, IMPL, GEN, P32>();
-  k_fused<T, NT, IMPL, GEN, P32><<<grid, NT, int(sizeof(FusedSmem<T, NT>)), s>>>(a);
+  k_fused<T, NT, IMPL, GEN, P32><<<grid, NT, fused_smem_size<T, NT>(), s>>>(a);
 }
 
 template <class T, int NT>
@@ -673,7 +702,7 @@ static int blocks_per_sm_nt() {
   configure_nt<T, NT, false>();
   int n = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused<T, NT, false, false, false>, NT,
-                                                int(sizeof(FusedSmem<T, NT>)));
+                                                fused_smem_size<T, NT>());
   return n;
 }
 
@@ -688,9 +717,9 @@ template <class T> int fused_blocks_per_sm(int nt) {
 
 template <class T> int fused_smem_bytes(int nt) {
   switch (nt) {
-    case 64: return int(sizeof(FusedSmem<T, 64>));
-    case 128: return int(sizeof(FusedSmem<T, 128>));
-    case 256: return int(sizeof(FusedSmem<T, 256>));
+    case 64: return fused_smem_size<T, 64>();
+    case 128: return fused_smem_size<T, 128>();
+    case 256: return fused_smem_size<T, 256>();
   }
   return -1;
 }

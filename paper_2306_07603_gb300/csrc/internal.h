@@ -35,6 +35,11 @@ struct CavDev {
   int pow32;                // FP32 storage only: 1 power law (and implicit solve) in FP32
   int pad_;
   double lid_ux, lid_uy;    // lid velocity (U, 0) on the trapezoid, U along the top edge in general
+  // pow_tab (FP32 argument, FP64 result) of Eq. (1.4): binomial coefficients
+  // b2 = m (m-1)/2 and, as floats, b3..b5 of (1 + t)^m with m = half_nm1; and
+  // the clamp of the FP32 strain rate, max(largest float <= gamma_min^2, FLT_MIN)
+  double pb2;
+  float pb3, pb4, pb5, gmin2_f;
 };
 
 // 1-D metric arrays of the trapezoid map (Eq. 3.8.2), per cavity at goff:
@@ -59,7 +64,7 @@ struct Geo {
 // Device buffers of a handle. T is double (FP64) or float (FP32DEV).
 struct Bufs {
   void *g[2];        // 9 planes per cavity: f-hat deviation g_i, ping-pong
-  double *lam[2];    // 1 plane per cavity: relaxation time, ping-pong
+  void *lam[2];      // 1 plane per cavity: relaxation time (storage type T), ping-pong
   void *fb;          // 9 planes: f-bar^+ (staged kernels)
   void *fp;          // 9 planes: f-hat^+ (staged kernels)
   void *fh;          // 9 planes: f(t + dt/2) (staged kernels)
@@ -71,6 +76,7 @@ struct Bufs {
   CavDev *cav;       // [ncav]
   Geo geo;
   double *powtab;    // tables of pow_fast (fastpow.cuh)
+  double *powt;      // [ncav][POWT_SIZE] per-cavity tables of pow_tab (fastpow.cuh)
   double *pref;      // [ncav] reference pressure: f-hat = w rho0 + wbar pref / c_s^2 + g
   int *cav_done;     // [ncav] fused kernel: tasks finished in the current step
   double *ptile;     // [ntiles + ncav] scratch of the re-basing reduction
@@ -82,13 +88,14 @@ struct StepArgs {
   const int *tile_cav;
   const void *g_in;
   void *g_out;
-  const double *lam_in;
-  double *lam_out;
+  const void *lam_in;  // relaxation-time planes in the storage type T
+  void *lam_out;
   void *fb, *fp, *fh;
   double *m0;
   double *part;
   unsigned *status;
   const double *powtab;
+  const double *powt;  // [ncav][POWT_SIZE] tables of pow_tab
   const double *pref;  // [ncav] reference pressure of the stored deviations
   int want_residual;
 };
@@ -98,6 +105,9 @@ struct StepArgs {
 struct Task {
   int cav, i0, i1, j0, j1, pad0, pad1, pad2;
 };
+
+// Bytes of one TMA tensor map (CUtensorMap) in device memory (64-byte aligned).
+constexpr int TMAP_BYTES = 128;
 
 struct FusedArgs {
   const CavDev *cav;
@@ -109,11 +119,13 @@ struct FusedArgs {
   int schedule;       // 0 grid (one CTA per task), 1 persistent static, 2 persistent dynamic
   const void *g_in;
   void *g_out;
-  const double *lam_in;
-  double *lam_out;
+  const void *tmap_in;  // [ncav] tensor maps of g_in (TMAP_BYTES each): box 32 x 1 x 9
+  const void *lam_in;  // relaxation-time planes in the storage type T
+  void *lam_out;
   double *part;
   unsigned *status;
   const double *powtab;
+  const double *powt;  // [ncav][POWT_SIZE] tables of pow_tab
   const double *pref;  // [ncav] reference pressure of the stored deviations
   int *cav_done;       // [ncav] tasks of the step finished (zero between steps)
   int implicit;        // 1: implicit form of Eq. (2.14) (kernel variant), 0: lagged
@@ -157,8 +169,11 @@ void launch_adjoint_seed_psi(const AdjArgs &a, int ntiles, int ncav, double *dpa
                              cudaStream_t s);
 void launch_adjoint_step(const AdjArgs &a, int ntiles, int ncav, double *dparams, cudaStream_t s);
 
-// Host-built tables of pow_fast (capi.cu) and its self-test (staged.cu)
+// Host-built tables of pow_fast and of pow_tab (capi.cu) and their self-tests (staged.cu)
 void fill_pow_tables(double *tab);
+void fill_cavity_pow_table(double *tab, double m, double C);
+void launch_pow_tab_selftest(int n, const double *x, double m, double C, const double *tab,
+                             double b2, float b3, float b4, float b5, double *out, cudaStream_t s);
 void launch_pow_f32_selftest(int n, const double *x, double m, double *out, cudaStream_t s);
 
 // Metrics of the bilinear map of a general quadrilateral at (xi, eta),
@@ -188,7 +203,7 @@ void launch_pow_selftest(int n, const double *x, double m, const double *tab, do
                          double *ref, cudaStream_t s);
 
 // Utility kernels (staged.cu)
-template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,
+template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, void *lam,
                                     int ntiles, cudaStream_t s);
 template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const double *pref,
                                       const void *g,
@@ -196,10 +211,10 @@ template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, co
                                       int nx, int ny, cudaStream_t s);
 template <class T> void launch_export(const CavDev *cav, int cavity, const double *pref,
                                       const void *g,
-                                      const double *lam, double *fhat, double *lamo, int nx,
+                                      const void *lam, double *fhat, double *lamo, int nx,
                                       int ny, cudaStream_t s);
 template <class T> void launch_import(const CavDev *cav, int cavity, const double *pref,
-                                      void *g, double *lam,
+                                      void *g, void *lam,
                                       const double *fhat, const double *lami, int nx, int ny,
                                       cudaStream_t s);
 // u, v, P at probe nodes [n][3] = (cavity, i, j) into out [n][3] (NaN for a

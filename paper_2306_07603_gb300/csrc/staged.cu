@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_collide(StepArgs a) {
   const int64_t b9 = 9 * cv.off;
   T g[9];
   load9((const T *)a.g_in + b9, cv.plane, node, g);
-  const double lam_prev = a.lam_in[cv.off + node];
+  const double lam_prev = double(((const T *)a.lam_in)[cv.off + node]);
 
   const T c = T(cv.c), cs2 = T(cv.cs2), ics2 = T(cv.inv_cs2);
   T ux, uy, P;
@@ -80,10 +80,11 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_collide(StepArgs a) {
   for (int q = 0; q < 9; ++q) d[q] = g[q] - geq[q];
   T pxx, pxy, pyy;
   second_moments(d, c, pxx, pxy, pyy);
-  const double lam = relaxation_time(pxx, pxy, pyy, lam_prev, cv, a.powtab);
-  a.lam_out[cv.off + node] = lam;                // lam(t), also next lam_prev
-
+  const double lam = relaxation_time(pxx, pxy, pyy, lam_prev, cv, a.powtab,
+                                     a.powt + int64_t(r.cav) * POWT_SIZE);
   const T L = T(lam), dt = T(cv.dt);
+  ((T *)a.lam_out)[cv.off + node] = L;           // lam(t), also next lam_prev
+
   const T i2 = T(1) / (T(2) * L + dt);
   const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
   const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt), (4 lam - dt)/(4 lam + 2 dt) = 1 - bb
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   const int64_t b9 = 9 * cv.off;
   const T *fb = (const T *)a.fb + b9;
   const int64_t node = int64_t(jj) * cv.pitch + ii;
-  const double lam = a.lam_out[cv.off + node];
+  const T lam = ((const T *)a.lam_out)[cv.off + node];
 
   const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
   const T hdt = T(0.5 * cv.dt);
@@ -280,7 +281,7 @@ __global__ void k_residual_reduce(const CavDev *cavs, const double *part, double
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_init(const CavDev *cavs, const int *tile_cav,
-                                                          T *g, double *lam) {
+                                                          T *g, T *lam) {
   const NodeRef r = tile_node(tile_cav, cavs);
   if (!r.valid) return;
   const CavDev &cv = cavs[r.cav];
@@ -290,22 +291,32 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_init(const CavDev *cavs, con
   equilibrium(T(0), lid ? T(cv.lid_ux) : T(0), lid ? T(cv.lid_uy) : T(0), T(cv.c),
               T(cv.inv_cs2), geq);
   store9(g + 9 * cv.off, cv.plane, node, geq);
-  lam[cv.off + node] = cv.lam0;
+  lam[cv.off + node] = T(cv.lam0);
 }
 
-// One thread per xi = const line: macros at every node, then
-// psi_j = psi_{j-1} + (I_j + I_{j-1}) deta / 2 with I = u y_eta - v x_eta.
+// Macros at every node and the stream function. A block is 32 xi = const
+// lines x MSEG row segments. Pass 1: rho, u, v and the integrand
+// I = u y_eta - v x_eta at every node (I parked in psi). Pass 2: each thread
+// sums the trapezoid intervals (I_j + I_{j-1}) deta / 2 of its segment. The
+// segment sums are scanned in a fixed order in shared memory, and pass 3
+// writes psi_j = psi_{j-1} + (I_j + I_{j-1}) deta / 2 from the segment's
+// offset (psi = 0 on the bottom wall).
+constexpr int MSEG = 32;
+
 template <class T>
-__global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *pref, const T *g,
-                         double *rho, double *u, double *v, double *psi) {
+__global__ void __launch_bounds__(32 * MSEG)
+    k_macros(const CavDev *cavs, Geo geo, int cavity, const double *pref, const T *g,
+             double *rho, double *u, double *v, double *psi) {
   const CavDev &cv = cavs[cavity];
   const double p0 = pref[cavity];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cv.nx) return;
+  const int i = blockIdx.x * 32 + threadIdx.x;
+  const int seg = (cv.ny + MSEG - 1) / MSEG;
+  const int j0 = threadIdx.y * seg, j1 = min(cv.ny, j0 + seg);
+  const bool col = i < cv.nx;
   const T *gb = g + 9 * cv.off;
   const double *gm = cv.general ? geo.gmet + 7 * cv.off : nullptr;
-  double acc = 0.0, Iprev = 0.0;
-  for (int j = 0; j < cv.ny; ++j) {
+  __shared__ double part[MSEG][32];
+  for (int j = j0; col && j < j1; ++j) {
     T gg[9];
     load9(gb, cv.plane, int64_t(j) * cv.pitch + i, gg);
     T ux, uy, P;
@@ -315,11 +326,32 @@ __global__ void k_macros(const CavDev *cavs, Geo geo, int cavity, const double *
     if (u) u[o] = double(ux);
     if (v) v[o] = double(uy);
     const int64_t nd = int64_t(j) * cv.pitch + i;
-    const double I = cv.general ? double(ux) * gm[5 * cv.plane + nd] - double(uy) * gm[4 * cv.plane + nd]
-                                : double(ux) * cv.H - double(uy) * geo.xeta[cv.goff + i];
+    if (psi)
+      psi[o] = cv.general ? double(ux) * gm[5 * cv.plane + nd] - double(uy) * gm[4 * cv.plane + nd]
+                          : double(ux) * cv.H - double(uy) * geo.xeta[cv.goff + i];
+  }
+  if (!psi) return;  // uniform over the launch
+  __syncthreads();   // every integrand of the block's lines is written
+  double sum = 0.0, Iprev = 0.0;
+  if (col && j0 < j1) {
+    Iprev = j0 > 0 ? psi[int64_t(j0 - 1) * cv.nx + i] : 0.0;
+    double Ip = Iprev;
+    for (int j = j0; j < j1; ++j) {
+      const double I = psi[int64_t(j) * cv.nx + i];
+      if (j > 0) sum += 0.5 * (I + Ip) * cv.deta;
+      Ip = I;
+    }
+  }
+  part[threadIdx.y][threadIdx.x] = sum;
+  __syncthreads();   // segment sums published; every integrand has been read
+  double acc = 0.0;
+  for (int k = 0; k < int(threadIdx.y); ++k) acc += part[k][threadIdx.x];
+  for (int j = j0; col && j < j1; ++j) {
+    const int64_t o = int64_t(j) * cv.nx + i;
+    const double I = psi[o];
     if (j > 0) acc += 0.5 * (I + Iprev) * cv.deta;
     Iprev = I;
-    if (psi) psi[o] = acc;
+    psi[o] = acc;
   }
 }
 
@@ -348,7 +380,7 @@ __global__ void k_probe(const CavDev *cavs, int ncav, const double *pref, const 
 
 template <class T>
 __global__ void k_export(const CavDev *cavs, int cavity, const double *pref, const T *g,
-                         const double *lam, double *fhat, double *lamo) {
+                         const T *lam, double *fhat, double *lamo) {
   const CavDev &cv = cavs[cavity];
   const double pt = pref[cavity] * cv.inv_cs2;
   const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -360,11 +392,11 @@ __global__ void k_export(const CavDev *cavs, int cavity, const double *pref, con
     for (int q = 0; q < 9; ++q)
       fhat[q * n2 + o] = double(g[9 * cv.off + q * cv.plane + node]) + wgt(q) * cv.rho0 +
                          wbar(q) * pt;
-  if (lamo) lamo[o] = lam[cv.off + node];
+  if (lamo) lamo[o] = double(lam[cv.off + node]);
 }
 
 template <class T>
-__global__ void k_import(const CavDev *cavs, int cavity, const double *pref, T *g, double *lam,
+__global__ void k_import(const CavDev *cavs, int cavity, const double *pref, T *g, T *lam,
                          const double *fhat, const double *lami) {
   const CavDev &cv = cavs[cavity];
   const double pt = pref[cavity] * cv.inv_cs2;
@@ -375,7 +407,7 @@ __global__ void k_import(const CavDev *cavs, int cavity, const double *pref, T *
 #pragma unroll
   for (int q = 0; q < 9; ++q)
     g[9 * cv.off + q * cv.plane + node] = T(fhat[q * n2 + o] - wgt(q) * cv.rho0 - wbar(q) * pt);
-  lam[cv.off + node] = lami[o];
+  lam[cv.off + node] = T(lami[o]);
 }
 
 // Re-basing of the stored deviations on the mean pressure (FP32 storage):
@@ -456,6 +488,23 @@ void launch_pow_selftest(int n, const double *x, double m, const double *tab, do
   k_pow_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, tab, fast, ref);
 }
 
+// pow_tab on the FP32 roundings of x (tab: a cavity table of exponent m and
+// factor C); out[k] = pow_tab(float(x[k])) and out[n + k] = C * CUDA's
+// pow(double(float(x[k])), m).
+__global__ void k_pow_tab_selftest(int n, const double *x, double m, double C, const double *tab,
+                                   double b2, float b3, float b4, float b5, double *out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const float xf = float(x[k]);
+  out[k] = pow_tab(xf, tab, m, b2, b3, b4, b5);
+  out[n + k] = C * pow(double(xf), m);
+}
+
+void launch_pow_tab_selftest(int n, const double *x, double m, double C, const double *tab,
+                             double b2, float b3, float b4, float b5, double *out, cudaStream_t s) {
+  k_pow_tab_selftest<<<(n + 255) / 256, 256, 0, s>>>(n, x, m, C, tab, b2, b3, b4, b5, out);
+}
+
 __global__ void k_pow_f32_selftest(int n, const double *x, double m, double *out) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
@@ -511,28 +560,28 @@ void launch_residual_reduce(const CavDev *cav, const double *part, double *resid
                             cudaStream_t s) {
   k_residual_reduce<<<ncav, 256, 0, s>>>(cav, part, resid);
 }
-template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, double *lam,
+template <class T> void launch_init(const CavDev *cav, const int *tile_cav, void *g, void *lam,
                                     int ntiles, cudaStream_t s) {
-  k_init<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (T *)g, lam);
+  k_init<T><<<ntiles, kTile, 0, s>>>(cav, tile_cav, (T *)g, (T *)lam);
 }
 template <class T> void launch_macros(const CavDev *cav, Geo geo, int cavity, const double *pref,
                                       const void *g, double *rho, double *u, double *v,
                                       double *psi, int nx, int ny, cudaStream_t s) {
   (void)ny;
-  k_macros<T><<<(nx + 127) / 128, 128, 0, s>>>(cav, geo, cavity, pref, (const T *)g, rho, u, v,
-                                                psi);
+  k_macros<T><<<(nx + 31) / 32, dim3(32, MSEG), 0, s>>>(cav, geo, cavity, pref, (const T *)g,
+                                                        rho, u, v, psi);
 }
 template <class T> void launch_export(const CavDev *cav, int cavity, const double *pref,
-                                      const void *g, const double *lam, double *fhat,
+                                      const void *g, const void *lam, double *fhat,
                                       double *lamo, int nx, int ny, cudaStream_t s) {
-  k_export<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (const T *)g, lam,
-                                                          fhat, lamo);
+  k_export<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (const T *)g,
+                                                          (const T *)lam, fhat, lamo);
 }
 template <class T> void launch_import(const CavDev *cav, int cavity, const double *pref, void *g,
-                                      double *lam, const double *fhat, const double *lami,
+                                      void *lam, const double *fhat, const double *lami,
                                       int nx, int ny, cudaStream_t s) {
-  k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (T *)g, lam, fhat,
-                                                          lami);
+  k_import<T><<<dim3((nx + 127) / 128, ny), 128, 0, s>>>(cav, cavity, pref, (T *)g, (T *)lam,
+                                                          fhat, lami);
 }
 template <class T> void launch_probe(const CavDev *cav, int ncav, const double *pref, const void *g,
                                      int n, const int *probes, double *out, cudaStream_t s) {
@@ -550,14 +599,14 @@ template <class T> void launch_rebase(const CavDev *cav, const int *tile_cav, vo
   template void launch_collide<T>(const StepArgs &, int, cudaStream_t);                       \
   template void launch_half<T>(const StepArgs &, int, cudaStream_t);                          \
   template void launch_full<T>(const StepArgs &, int, cudaStream_t);                          \
-  template void launch_init<T>(const CavDev *, const int *, void *, double *, int,            \
+  template void launch_init<T>(const CavDev *, const int *, void *, void *, int,              \
                                cudaStream_t);                                                  \
   template void launch_macros<T>(const CavDev *, Geo, int, const double *, const void *,      \
                                  double *, double *, double *, double *, int, int,            \
                                  cudaStream_t);                                               \
   template void launch_export<T>(const CavDev *, int, const double *, const void *,           \
-                                 const double *, double *, double *, int, int, cudaStream_t); \
-  template void launch_import<T>(const CavDev *, int, const double *, void *, double *,       \
+                                 const void *, double *, double *, int, int, cudaStream_t);   \
+  template void launch_import<T>(const CavDev *, int, const double *, void *, void *,         \
                                  const double *, const double *, int, int, cudaStream_t);     \
   template void launch_probe<T>(const CavDev *, int, const double *, const void *, int,       \
                                 const int *, double *, cudaStream_t);                         \

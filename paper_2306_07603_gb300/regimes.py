@@ -29,6 +29,8 @@ recorded series are formed here.
     python -m paper_2306_07603_gb300.regimes --cases theta60     # Sec. 5.3, theta = 60 deg
     python -m paper_2306_07603_gb300.regimes --case 257,60,1.5,4000 --precision fp64
     python -m paper_2306_07603_gb300.regimes --workload unsteady1025
+    python -m paper_2306_07603_gb300.regimes --workload unsteady1025 --compare-precisions \
+        --transient 50000 --steps 100000
 """
 from __future__ import annotations
 
@@ -154,6 +156,41 @@ def summarize(specs, rec, probes=PROBES, **kw):
     return rows
 
 
+def _rel(a, b):
+    return float(abs(a - b) / abs(b)) if b != 0 else float(abs(a - b))
+
+
+def compare_precisions(specs, transient, steps, every=100, **opts):
+    """The same cavities and window in the FP64 form and the FP32-deviation
+    form: per cavity, the mean, variance and principal period of E(t) and the
+    mean and variance of u, v at every probe in both, and their relative
+    differences (FP32 against FP64). Returns (rows, seconds per form)."""
+    rec = {p: record(specs, p, transient, steps, every, **opts) for p in ("fp64", "fp32dev")}
+    sm = {p: summarize(specs, rec[p]) for p in rec}
+    rows = []
+    for k, c in enumerate(specs):
+        a, b = sm["fp32dev"][k], sm["fp64"][k]
+        d = {"E_mean": _rel(a["E_mean"], b["E_mean"]), "E_var": _rel(a["E_var"], b["E_var"]),
+             "period": (_rel(a["period"], b["period"])
+                        if a["period"] and b["period"] else None)}
+        e64 = rec["fp64"]["energy"][:, k]
+        e32 = rec["fp32dev"]["energy"][:, k]
+        d["E_series_max"] = float(np.abs(e32 - e64).max() / np.abs(e64).max())
+        pr = []
+        for q in range(len(a["probes"])):
+            pa, pb = a["probes"][q], b["probes"][q]
+            scale = max(abs(pb["u_mean"]), abs(pb["v_mean"]), 1e-30)
+            pr.append({"xi": pb["xi"], "eta": pb["eta"],
+                       "u_mean": abs(pa["u_mean"] - pb["u_mean"]) / scale,
+                       "v_mean": abs(pa["v_mean"] - pb["v_mean"]) / scale,
+                       "u_std": _rel(pa["u_var"] ** 0.5, pb["u_var"] ** 0.5),
+                       "v_std": _rel(pa["v_var"] ** 0.5, pb["v_var"] ** 0.5)})
+        d["probes"] = pr
+        rows.append({"grid": f"{c.nx}x{c.ny}", "theta": getattr(c, "theta_deg", None), "n": c.n,
+                     "Re": c.Re, "fp64": b, "fp32dev": a, "difference": d})
+    return rows, {p: round(rec[p]["seconds"], 1) for p in rec}
+
+
 def main(argv=None):
     p = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     p.add_argument("--cases", choices=["theta60"], default=None)
@@ -167,6 +204,9 @@ def main(argv=None):
     p.add_argument("--eta-b", type=float, default=None, help="blend of Eq. 2.5 (default 0.5)")
     p.add_argument("--only", default=None,
                    help="with --cases: comma-separated indices of the cases to run")
+    p.add_argument("--compare-precisions", action="store_true",
+                   help="run the window in FP64 and in the FP32-deviation form and report "
+                        "the differences of the statistics")
     a = p.parse_args(argv)
     if a.case:
         N, th, n, Re = (float(v) for v in a.case.split(","))
@@ -179,6 +219,12 @@ def main(argv=None):
             specs = [specs[int(k)] for k in a.only.split(",")]
     if a.eta_b is not None:
         opts["eta_b"] = a.eta_b
+    if a.compare_precisions:
+        rows, secs = compare_precisions(specs, a.transient, a.steps, a.every, **opts)
+        print(json.dumps({"compare": "fp32dev vs fp64", "eta_b": opts.get("eta_b", 0.5),
+                          "transient": a.transient, "steps": a.steps, "every": a.every,
+                          "seconds": secs, "cases": rows}))
+        return
     rec = record(specs, a.precision, a.transient, a.steps, a.every, **opts)
     if a.save:
         np.savez_compressed(a.save, probes=rec["probes"], energy=rec["energy"],

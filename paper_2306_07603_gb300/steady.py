@@ -10,8 +10,10 @@ own steady state along the slowest cavity mode, so for the cavities whose
 FP64 run did reach ``tol`` (steady) the error is also reported after the
 longer run, where it has levelled off. Fields: u, v, psi, and P minus its
 mean (the mean pressure is a neutral mode of the scheme); error =
-max|a - b| / max|b|. Both runs use the library only; the FP64 form is the
-one whose steps match the oracle to 1e-12.
+max|a - b| / max|b|. Cavities whose FP64 run does not settle are also
+compared by their time-mean fields over a common window (``--window``).
+Both runs use the library only; the FP64 form is the one whose steps match
+the oracle to 1e-12.
 
     python -m paper_2306_07603_gb300.steady --workload sweep257
 """
@@ -48,21 +50,46 @@ def _errors(a, b):
     return err
 
 
+def _mean_fields(s, ncav, steps, every):
+    """Advances `steps` steps, sampling the fields every `every` steps; returns
+    their time means (u, v, psi, P) per cavity."""
+    acc = None
+    n = 0
+    for _ in range(steps // every):
+        s.step(every)
+        f = _fields(s, ncav)
+        if acc is None:
+            acc = [{q: m[q].copy() for q in ("u", "v", "psi", "P")} for m in f]
+        else:
+            for a, m in zip(acc, f):
+                for q in a:
+                    a[q] += m[q]
+        n += 1
+    return [{q: a[q] / n for q in a} for a in acc]
+
+
 def compare(workload="sweep257", tol=1e-8, max_steps=200000, chunk=2000, kernel="auto",
-            fp32_factor=3):
+            fp32_factor=3, window=0, every=1000):
+    """FP64 run to `tol` (or `max_steps`), then the FP32-deviation run (see the
+    module docstring). With `window` > 0, the cavities whose FP64 run did not
+    reach `tol` are also compared by their time-mean fields over the window of
+    `window` steps that follows, sampled every `every` steps, in both forms."""
     specs = WORKLOADS[workload]()
     opts = dict(WORKLOAD_OPTIONS.get(workload, {}), kernel=kernel)
     s = _solver(specs, "fp64", **opts)
     steps, t0 = 0, time.time()
+    hist64 = []
     while True:
         s.step(chunk)
         steps += chunk
         r64 = [float(row[2]) for row in s.residual()]
+        hist64.append((steps, max(r64)))
         if max(r64) < tol or steps >= max_steps:
             break
     s.sync()
-    w64 = time.time() - t0
     f64 = _fields(s, len(specs))
+    mean64 = _mean_fields(s, len(specs), window, every) if window else None
+    w64 = time.time() - t0
     s.close()
 
     s = _solver(specs, "fp32dev", **opts)
@@ -70,7 +97,8 @@ def compare(workload="sweep257", tol=1e-8, max_steps=200000, chunk=2000, kernel=
     s.step(steps)
     f32 = _fields(s, len(specs))
     equal = [_errors(f32[k], f64[k]) for k in range(len(specs))]
-    s.step((fp32_factor - 1) * steps)
+    mean32 = _mean_fields(s, len(specs), window, every) if window else None
+    s.step(max(0, (fp32_factor - 1) * steps - window))
     f32 = _fields(s, len(specs))
     w32 = time.time() - t0
     r32 = [float(row[2]) for row in s.residual()]
@@ -81,14 +109,18 @@ def compare(workload="sweep257", tol=1e-8, max_steps=200000, chunk=2000, kernel=
         rows.append({"grid": f"{c.nx}x{c.ny}", "theta": c.theta_deg, "n": c.n, "Re": c.Re,
                      "fp64_rinf": r64[k], "fp64_steady": steady, "fp32_rinf": r32[k],
                      "error_equal_steps": equal[k],
-                     "error_steady": _errors(f32[k], f64[k]) if steady else None})
+                     "error_steady": _errors(f32[k], f64[k]) if steady else None,
+                     "error_time_mean": (_errors(mean32[k], mean64[k])
+                                         if (window and not steady) else None)})
     worst = {q: max(r["error_equal_steps"][q] for r in rows) for q in equal[0]}
     st = [r["error_steady"] for r in rows if r["error_steady"] is not None]
     worst_steady = {q: max(e[q] for e in st) for q in st[0]} if st else None
     return {"workload": workload, "tol": tol, "fp64_steps": steps,
-            "fp32dev_steps": fp32_factor * steps, "fp64_seconds": round(w64, 2),
+            "fp32dev_steps": max(fp32_factor * steps, steps + window),
+            "window": window, "every": every, "fp64_seconds": round(w64, 2),
             "fp32dev_seconds": round(w32, 2), "max_error_equal_steps": worst,
-            "max_error_steady": worst_steady, "cavities": rows}
+            "max_error_steady": worst_steady, "fp64_rinf_history": hist64[::10],
+            "cavities": rows}
 
 
 def main(argv=None):
@@ -99,8 +131,17 @@ def main(argv=None):
     p.add_argument("--chunk", type=int, default=2000)
     p.add_argument("--kernel", default="auto", choices=["auto", "staged", "fused"])
     p.add_argument("--fp32-factor", type=int, default=3)
+    p.add_argument("--window", type=int, default=0,
+                   help="steps of the time-mean comparison of the cavities that do not settle")
+    p.add_argument("--every", type=int, default=1000)
+    p.add_argument("--save", default=None, help="also write the result to this JSON file")
     a = p.parse_args(argv)
-    print(json.dumps(compare(a.workload, a.tol, a.max_steps, a.chunk, a.kernel, a.fp32_factor)))
+    out = compare(a.workload, a.tol, a.max_steps, a.chunk, a.kernel, a.fp32_factor, a.window,
+                  a.every)
+    if a.save:
+        with open(a.save, "w") as f:
+            json.dump(out, f, indent=1)
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -50,7 +50,7 @@ def test_reduce_over_ranks_gloo_world2():
 def test_defaults_finish_quickly():
     import bench
     a = bench.parse_args([])
-    assert a.gpus == 1 and a.warmup >= 3 and a.workload == "sweep257"
+    assert a.gpus == 1 and a.warmup >= 3 and a.workload == "batch64"
 
 
 def test_reference_arm_json_contract():
