@@ -71,21 +71,10 @@ constexpr int fused_smem_size() {
 
 __device__ __forceinline__ int slot6(int r) { return (r + 12) % RING; }
 
-// Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side known
-// at compile time (eta direction: the side is the sign of e_iy, since
-// c_{i eta} = c e_iy / H); `edge` selects the first-order near-wall form.
-template <bool POS, class T>
-__device__ __forceinline__ T dmix2_side(T fm2, T fm1, T f0, T fp1, T fp2, bool edge, T eta_b) {
-  T up;
-  if (POS)
-    up = edge ? T(2) * (f0 - fm1) : (T(3) * f0 - T(4) * fm1 + fm2);
-  else
-    up = edge ? T(2) * (fp1 - f0) : -(T(3) * f0 - T(4) * fp1 + fp2);
-  return eta_b * (fp1 - fm1) + (T(1) - eta_b) * up;
-}
-
-// The same with the side chosen at run time (xi direction): the upwind
-// operands are selected, then one stencil is evaluated.
+// Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side chosen
+// at run time (general quadrilaterals): the upwind operands are selected,
+// then one stencil is evaluated; `edge_pos` / `edge_neg` select the
+// first-order near-wall form on either side.
 template <class T>
 __device__ __forceinline__ T dmix2_sel(T fm2, T fm1, T f0, T fp1, T fp2, bool pos, bool edge_pos,
                                        bool edge_neg, T eta_b) {
@@ -95,40 +84,60 @@ __device__ __forceinline__ T dmix2_sel(T fm2, T fm1, T f0, T fp1, T fp2, bool po
   return eta_b * (fp1 - fm1) + (T(1) - eta_b) * (pos ? u : -u);
 }
 
-// c_{q xi} D_xi F + c_{q eta} D_eta F at an interior node: `row` is the xi
-// row of plane q (this thread at column lane l), `col` the five eta neighbours.
-template <int Q, class T>
-__device__ __forceinline__ T advect_q(const T *row, int l, const T col[5], T A, T B, T ceta_unit,
-                                      bool clo, bool chi, bool lo, bool hi, T eta_b, T i2dxi,
-                                      T i2deta) {
-  const T cxi = T(ex(Q)) * A - T(ey(Q)) * B;
-  const T f0 = col[2];
-  T adv = cxi * dmix2_sel(row[l - 2], row[l - 1], f0, row[l + 1], row[l + 2], cxi >= T(0), clo,
-                          chi, eta_b) * i2dxi;
-  if constexpr (ey(Q) != 0) {
-    const T ceta = T(ey(Q)) * ceta_unit;
-    const T dy = (ey(Q) > 0) ? dmix2_side<true>(col[0], col[1], f0, col[3], col[4], lo, eta_b)
-                             : dmix2_side<false>(col[0], col[1], f0, col[3], col[4], hi, eta_b);
-    adv += ceta * dy * i2deta;
-  }
-  return adv;
+// The mixed difference of Eqs. (2.5)-(2.7) times 2 d, for the side "from
+// below" (c >= 0) with a = F[k+1], b = F[k-1], cf = F[k-2], and for the side
+// from above with a = F[k-1], b = F[k+1], cf = F[k+2], is
+//   sigma [eta_b (a - b) + (1 - eta_b) (3 (F[k] - b) + (cf - b))],
+// sigma = +1 and -1: both branches of Eq. (2.7) in one expression of the
+// selected operands. Next to a wall the far upwind node cf is replaced by the
+// linear extrapolation 2 b - F[k], which is the first-order near-wall
+// difference (then cf - b = -(F[k] - b)). Differences are formed before they
+// are scaled, so that a constant field gives exactly zero in any precision.
+template <class T>
+__device__ __forceinline__ T mixed_sum(T a, T b, T cf, T f0, bool edge, T kb, T ku3, T ku) {
+  const T d2 = f0 - b;
+  const T d3 = edge ? -d2 : cf - b;
+  return kb * (a - b) + (ku3 * d2 + ku * d3);
 }
 
-// out[q] = base_q - scale * advection_q for q = Q..8; ring planes are RS
-// apart, base planes BS apart.
+// base_q - scale (c_{q xi} D_xi F + c_{q eta} D_eta F) at an interior node of
+// the trapezoid (Eq. 3.7 with scale = dt/2, Eq. 3.6 with scale = dt):
+// `row` is the xi row of plane q at this thread's lane l, `col` the five eta
+// neighbours. xs = scale c_{q xi} / (2 dxi) = e_x As - e_y Bs, whose sign is
+// the upwind side along xi (it absorbs sigma: xs D = |xs| sum); along eta the
+// side is the sign of e_y (c_{q eta} = c e_y / H) and the factor is
+// Es = scale (c / H) / (2 deta).
+template <int Q, class T>
+__device__ __forceinline__ T advect_out(T base, const T *row, int l, const T col[5], T As, T Bs,
+                                        T Es, bool clo, bool chi, bool lo, bool hi, T kb, T ku3,
+                                        T ku) {
+  const T xs = T(ex(Q)) * As - T(ey(Q)) * Bs;
+  const T f0 = col[2];
+  const T fm1 = row[l - 1], fp1 = row[l + 1];
+  const bool pos = xs >= T(0);
+  const T sx = mixed_sum(pos ? fp1 : fm1, pos ? fm1 : fp1, pos ? row[l - 2] : row[l + 2], f0,
+                         pos ? clo : chi, kb, ku3, ku);
+  T out = base - fabs(xs) * sx;
+  if constexpr (ey(Q) > 0)
+    out -= Es * mixed_sum(col[3], col[1], col[0], f0, lo, kb, ku3, ku);
+  else if constexpr (ey(Q) < 0)
+    out -= Es * mixed_sum(col[1], col[3], col[4], f0, hi, kb, ku3, ku);
+  return out;
+}
+
+// out[q] for q = Q..8; ring planes are RS apart, base planes BS apart.
 template <class T, int Q, int RS, int BS>
 struct AdvectAll {
-  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int l, T A, T B,
-                                             T ceta_unit, bool clo, bool chi, bool lo, bool hi,
-                                             T eta_b, T i2dxi, T i2deta, T scale, const T *base,
-                                             T out[9]) {
+  __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int l, T As,
+                                             T Bs, T Es, bool clo, bool chi, bool lo, bool hi,
+                                             T kb, T ku3, T ku, const T *base, T out[9]) {
     const T col[5] = {cols[0][Q * RS], cols[1][Q * RS], cols[2][Q * RS], cols[3][Q * RS],
                       cols[4][Q * RS]};
-    out[Q] = base[Q * BS] - scale * advect_q<Q>(rows + Q * RS, l, col, A, B, ceta_unit, clo, chi,
-                                                lo, hi, eta_b, i2dxi, i2deta);
+    out[Q] = advect_out<Q>(base[Q * BS], rows + Q * RS, l, col, As, Bs, Es, clo, chi, lo, hi, kb,
+                           ku3, ku);
     if constexpr (Q < 8)
-      AdvectAll<T, Q + 1, RS, BS>::run(rows, cols, l, A, B, ceta_unit, clo, chi, lo, hi, eta_b,
-                                       i2dxi, i2deta, scale, base, out);
+      AdvectAll<T, Q + 1, RS, BS>::run(rows, cols, l, As, Bs, Es, clo, chi, lo, hi, kb, ku3, ku,
+                                       base, out);
   }
 };
 
@@ -259,6 +268,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T eta_b = T(cv.eta_b);
   const T i2dxi = T(cv.inv2dxi), i2deta = T(cv.inv2deta);
   const T ceta_unit = T(cv.c / cv.H);
+  // factors of the trapezoid's advection (advect_out): scale / (2 dxi) and
+  // scale (c / H) / (2 deta) with scale = dt/2 (half step) and dt (full step);
+  // the blend weights of Eq. (2.5)
+  const T hxs = T(0.5 * cv.dt * cv.inv2dxi), fxs = T(cv.dt * cv.inv2dxi);
+  const T Es1 = T(0.5 * cv.dt * cv.inv2deta * cv.c / cv.H), Es2 = T(cv.dt * cv.inv2deta * cv.c / cv.H);
+  const T ku = T(1.0 - cv.eta_b), ku3 = T(3.0 * (1.0 - cv.eta_b));
   const T xeH = GEN ? T(0) : T(a.geo.xeH[goff + cc]);  // x_eta / H of this column
   // general quadrilateral (bilinear map): x_eta, y_eta of this column and
   // x_xi, y_xi of a row; the node's metrics follow from Eqs. (3.2)-(3.3)
@@ -443,10 +458,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
                                           iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, hdt,
                                           &S.fb[sm][0][l], fbar);  // Eq. (3.7)
         } else {
-          const T A = A1;                                // c xi_x of row m
-          const T B = A * xeH;                           // c xi_x x_eta / H
-          AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
-                                       eta_b, i2dxi, i2deta, hdt, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
+          const T As = A1 * hxs;                         // dt/2 c xi_x / (2 dxi) of row m
+          const T Bs = As * xeH;                         // ... times x_eta / H
+          AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, As, Bs, Es1, clo, chi, lo, hi,
+                                       eta_b, ku3, ku, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
         }
       }
       T ux, uy, P;
@@ -505,10 +520,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
                                           iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, dt,
                                           sfme + sp * SLOT, gnv);  // Eq. (3.6)
         } else {
-          const T A = A2;                                // c xi_x of row o
-          const T B = A * xeH;
-          AdvectAll<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, A, B, ceta_unit, clo, chi, lo, hi,
-                                       eta_b, i2dxi, i2deta, dt, sfme + sp * SLOT, gnv);  // Eq. (3.6)
+          const T As = A2 * fxs;                         // dt c xi_x / (2 dxi) of row o
+          const T Bs = As * xeH;
+          AdvectAll<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, As, Bs, Es2, clo, chi, lo, hi,
+                                       eta_b, ku3, ku, sfme + sp * SLOT, gnv);  // Eq. (3.6)
         }
       }
       if (clo || chi) {                                // values the wall columns extrapolate

@@ -202,6 +202,9 @@ def main(argv=None):
     p.add_argument("--every", type=int, default=100)
     p.add_argument("--save", default=None, help="write the raw series to this .npz")
     p.add_argument("--eta-b", type=float, default=None, help="blend of Eq. 2.5 (default 0.5)")
+    p.add_argument("--dt-mode", choices=["contravariant", "grid"], default=None,
+                   help="time-step rule (default contravariant)")
+    p.add_argument("--cfl", type=float, default=None, help="Courant number (default 0.5)")
     p.add_argument("--only", default=None,
                    help="with --cases: comma-separated indices of the cases to run")
     p.add_argument("--compare-precisions", action="store_true",
@@ -219,6 +222,10 @@ def main(argv=None):
             specs = [specs[int(k)] for k in a.only.split(",")]
     if a.eta_b is not None:
         opts["eta_b"] = a.eta_b
+    if a.dt_mode is not None:
+        opts["dt_mode"] = a.dt_mode
+    if a.cfl is not None:
+        opts["cfl"] = a.cfl
     if a.compare_precisions:
         rows, secs = compare_precisions(specs, a.transient, a.steps, a.every, **opts)
         print(json.dumps({"compare": "fp32dev vs fp64", "eta_b": opts.get("eta_b", 0.5),
@@ -230,6 +237,7 @@ def main(argv=None):
         np.savez_compressed(a.save, probes=rec["probes"], energy=rec["energy"],
                             dt=np.array(rec["dt"]), every=a.every)
     print(json.dumps({"precision": a.precision, "eta_b": opts.get("eta_b", 0.5),
+                      "dt_mode": opts.get("dt_mode", "contravariant"), "cfl": opts.get("cfl", 0.5),
                       "transient": a.transient, "steps": a.steps,
                       "every": a.every, "seconds": round(rec["seconds"], 1),
                       "mlups": round(rec["lattice_updates"] / rec["seconds"] / 1e6, 1),
