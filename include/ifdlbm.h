@@ -102,7 +102,17 @@ typedef struct {
                         on GB300's 1/64-rate FP64 pipe, but outside the FP32
                         deviation form, which keeps them in FP64. INVALID_ARG
                         with FP64. */
+  int wall_pressure; /* IFDLBM_WALLP_*: the pressure the wall rule (Sec. 4) puts in
+                        the wall node's equilibrium. ZEROTH (default): that of the
+                        inner neighbour. FIRST: 2 P_nb - P_nnb, extrapolated along
+                        the grid line through the next node (a reading the paper
+                        leaves open). FIRST runs on the staged kernels: kernel
+                        AUTO selects STAGED, FUSED is INVALID_ARG. */
 } ifdlbm_options;
+
+/* Pressure of the wall rule (ifdlbm_options.wall_pressure). */
+#define IFDLBM_WALLP_ZEROTH 0
+#define IFDLBM_WALLP_FIRST 1
 
 /* Time-step rules ("c = 1, CFL = 0.5", Sec. 5.1). */
 #define IFDLBM_DT_GRID 0          /* dt = cfl * min(L/(nx-1), H/(ny-1)) / c; on a skewed
@@ -402,7 +412,8 @@ int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best);
 
 /* Discrete adjoint (reverse mode) of the step, for gradients of a scalar
  * objective with respect to n, Re and theta (pattern "differentiation").
- * Needs a handle created with IFDLBM_FP64 and IFDLBM_KERNEL_STAGED. States
+ * Needs a handle created with IFDLBM_FP64 and IFDLBM_KERNEL_STAGED (and the
+ * lagged relaxation time and zeroth-order wall pressure it differentiates). States
  * and adjoints are DEVICE buffers of ifdlbm_state_bytes(h) bytes in the
  * layout of ifdlbm_save_state_dev (adjoint entry k is d J / d state entry k).
  * dparams is a DEVICE array [ncav][3] to which d J / d n, d J / d Re and

@@ -385,6 +385,7 @@ class Params:
     rho0: float = 1.0
     c: float = 1.0
     implicit_lambda: bool = False   # solve Eq. (2.14) at the current lam instead of lagging
+    wall_pressure: int = 0          # wall-rule pressure: 0 zeroth-order, 1 first-order extrapolation
 
 
 def cavity_grid(nx, ny, L=1.0, H=1.0, theta_deg=60.0, U=0.1, c=1.0):
@@ -494,7 +495,7 @@ def periodic_grid(nx, ny, Lx=1.0, Ly=1.0, periodic_eta=True, c=1.0):
 
 def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None,
                   gamma_min=None, dt=None, dt_mode="contravariant", grid=None,
-                  implicit_lambda=False):
+                  implicit_lambda=False, wall_pressure=0):
     """Parameters of a cavity run.
 
     * K from Re, Eq. (2.15.1).
@@ -529,7 +530,7 @@ def cavity_params(nx, ny, Re, n, U=0.1, H=1.0, L=1.0, cfl=0.5, c=1.0, eta_b=None
     if gamma_min is None:
         gamma_min = 1e-3 * U / H
     return Params(dt=dt, K=K, n=n, gamma_min=gamma_min, eta_b=eta_b, c=c,
-                  implicit_lambda=implicit_lambda)
+                  implicit_lambda=implicit_lambda, wall_pressure=wall_pressure)
 
 
 DEFAULT_ETA_B = 0.5
@@ -575,7 +576,10 @@ def nee_boundary(F, g: Grid, prm: Params):
 
     READING: the pressure is extrapolated at zeroth order (P_b = P_nb); the
     same rule is applied to f at t + dt/2 (needed by the full-step stencil)
-    and to f-hat at t + dt (Step 6).
+    and to f-hat at t + dt (Step 6). The alternative reading
+    prm.wall_pressure = 1 extrapolates it at first order along the same grid
+    line, P_b = 2 P_nb - P_nnb, nnb the next node beyond nb (the diagonal one
+    at corners); the non-equilibrium part is taken from nb as before.
     """
     nodes = _boundary_nodes(g)
     if not nodes:
@@ -588,7 +592,11 @@ def nee_boundary(F, g: Grid, prm: Params):
     uw_y = np.array([g.wall_u[b[0]][1][b[1]] for b in nodes])
     Fn = F[:, jn, inn]                                   # (9, n_boundary)
     ux_n, uy_n, P_n = macros(Fn, prm.rho0, prm.c)
-    fe_w = equilibrium(P_n, uw_x + 0.0 * P_n, uw_y + 0.0 * P_n, prm.rho0, prm.c)
+    P_b = P_n
+    if getattr(prm, "wall_pressure", 0) == 1:
+        P_nn = macros(F[:, 2 * jn - jb, 2 * inn - ib], prm.rho0, prm.c)[2]
+        P_b = 2.0 * P_n - P_nn
+    fe_w = equilibrium(P_b, uw_x + 0.0 * P_n, uw_y + 0.0 * P_n, prm.rho0, prm.c)
     fe_n = equilibrium(P_n, ux_n, uy_n, prm.rho0, prm.c)
     F[:, jb, ib] = fe_w + (Fn - fe_n)
     return F

@@ -36,6 +36,8 @@ IFDLBM_KPROF_COUNT = 5
 IFDLBM_STATIC_MAX_NODES = 2097152
 IFDLBM_LAMBDA_LAGGED = 0
 IFDLBM_LAMBDA_IMPLICIT = 1
+IFDLBM_WALLP_ZEROTH = 0
+IFDLBM_WALLP_FIRST = 1
 IFDLBM_DT_GRID = 0
 IFDLBM_DT_CONTRAVARIANT = 1
 IFDLBM_SCHED_GRID = 0
@@ -52,7 +54,8 @@ class ifdlbm_options(C.Structure):
                 ("gamma_min", C.c_double), ("dt", C.c_double), ("rho0", C.c_double),
                 ("precision", C.c_int), ("kernel", C.c_int), ("graph_chunk", C.c_int),
                 ("fused_threads", C.c_int), ("fused_rows", C.c_int), ("schedule", C.c_int),
-                ("dt_mode", C.c_int), ("lambda_mode", C.c_int), ("power_fp32", C.c_int)]
+                ("dt_mode", C.c_int), ("lambda_mode", C.c_int), ("power_fp32", C.c_int),
+                ("wall_pressure", C.c_int)]
 
 
 class ifdlbm_cavity(C.Structure):

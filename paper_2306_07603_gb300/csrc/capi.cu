@@ -518,6 +518,11 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown dt_mode");
   if (opt.lambda_mode != IFDLBM_LAMBDA_LAGGED && opt.lambda_mode != IFDLBM_LAMBDA_IMPLICIT)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown lambda_mode");
+  if (opt.wall_pressure != IFDLBM_WALLP_ZEROTH && opt.wall_pressure != IFDLBM_WALLP_FIRST)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: unknown wall_pressure");
+  if (opt.wall_pressure == IFDLBM_WALLP_FIRST && opt.kernel == IFDLBM_KERNEL_FUSED)
+    return fail(nullptr, IFDLBM_ERR_INVALID_ARG,
+                "options: the first-order wall pressure runs on the staged kernels");
   if (opt.power_fp32 != 0 && opt.power_fp32 != 1)
     return fail(nullptr, IFDLBM_ERR_INVALID_ARG, "options: power_fp32 must be 0 or 1");
   if (opt.power_fp32 && opt.precision != IFDLBM_FP32DEV)
@@ -563,7 +568,8 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->precision = opt.precision;
   h->kernel = opt.kernel != IFDLBM_KERNEL_AUTO
                   ? opt.kernel
-                  : (opt.precision == IFDLBM_FP32DEV && (!quads || quad_fused_ok)
+                  : (opt.precision == IFDLBM_FP32DEV && (!quads || quad_fused_ok) &&
+                             opt.wall_pressure == IFDLBM_WALLP_ZEROTH
                          ? IFDLBM_KERNEL_FUSED
                          : IFDLBM_KERNEL_STAGED);
   h->fused_nt = opt.fused_threads ? opt.fused_threads : 128;
@@ -604,6 +610,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
     cv.K = std::pow(s.U_lid, 2.0 - s.n) * std::pow(H, s.n) / s.Re;  // Eq. (2.15.1)
     cv.nm1 = s.n - 1.0;
     cv.implicit = opt.lambda_mode == IFDLBM_LAMBDA_IMPLICIT ? 1 : 0;
+    cv.wallp = opt.wall_pressure == IFDLBM_WALLP_FIRST ? 1 : 0;
     cv.pow32 = opt.power_fp32 ? 1 : 0;
     cv.gmin = opt.gamma_min > 0 ? opt.gamma_min : 1e-3 * s.U_lid / H;
     cv.dt = opt.dt > 0 ? opt.dt : opt.cfl * std::min(L / (s.nx - 1), H / (s.ny - 1)) / opt.c;
@@ -1263,6 +1270,8 @@ int adjoint_ready(ifdlbm_ctx *h) {
     return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the lagged relaxation time");
   if (!h->quad.empty())
     return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the trapezoid map of Eq. (3.8.1)");
+  if (h->opt.wall_pressure != IFDLBM_WALLP_ZEROTH)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "adjoint: differentiates the zeroth-order wall pressure");
   if (h->adj_g1) return IFDLBM_OK;
   const size_t P = size_t(h->total_plane) * sizeof(double);
   bool ok = true;

@@ -245,7 +245,21 @@ __device__ __forceinline__ double cxi_of(int q, double A, double B) {
   return double(ex(q)) * A - double(ey(q)) * B;
 }
 
-// Wall-node rule (Sec. 4): F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
+// Wall-node rule (Sec. 4) with a given wall pressure Pb:
+// F_b = f^eq(Pb, u_w) + F_nb - f^eq(P_nb, u_nb), F holding F_nb on entry.
+template <class T>
+__device__ __forceinline__ void nee_p(T F[9], T uwx, T uwy, T Pb, T c, T cs2, T ics2) {
+  T ux, uy, P;
+  moments(F, c, cs2, ux, uy, P);
+  T fw[9], fn[9];
+  equilibrium(Pb, uwx, uwy, c, ics2, fw);
+  equilibrium(P, ux, uy, c, ics2, fn);
+#pragma unroll
+  for (int q = 0; q < 9; ++q) F[q] = fw[q] + (F[q] - fn[q]);
+}
+
+// Wall-node rule (Sec. 4) with the pressure extrapolated at zeroth order:
+// F_b = f^eq(P_nb, u_w) + F_nb - f^eq(P_nb, u_nb).
 template <class T>
 __device__ __forceinline__ void nee(T F[9], T uwx, T uwy, T c, T cs2, T ics2) {
   T ux, uy, P;

@@ -33,7 +33,7 @@ struct CavDev {
   int implicit;             // 1: lambda from the implicit form of Eq. (2.14), 0: lagged
   int general;              // 1: general quadrilateral, per-node metrics in Geo::gmet
   int pow32;                // FP32 storage only: 1 power law (and implicit solve) in FP32
-  int pad_;
+  int wallp;                // wall rule's pressure: 0 zeroth-order, 1 first-order (staged)
   double lid_ux, lid_uy;    // lid velocity (U, 0) on the trapezoid, U along the top edge in general
   // pow_tab (FP32 argument, FP64 result) of Eq. (1.4): binomial coefficients
   // b2 = m (m-1)/2 and, as floats, b3..b5 of (1 + t)^m with m = half_nm1; and

@@ -171,20 +171,14 @@ __device__ __forceinline__ void contravariant(const NodeMetrics<GEN> &m, int q, 
 // ---------------------------------------------------------------------------
 // Step (4): half step and f(t + dt/2)
 // ---------------------------------------------------------------------------
+// f(t + dt/2) at interior node (ii, jj): the half step of Eq. (3.7) from
+// f-bar^+, then Eq. (2.17) with the node's lambda(t).
 template <class T, bool GEN>
-__global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
-  const NodeRef r = tile_node(a.tile_cav, a.cav);
-  if (!r.valid) return;
-  const CavDev &cv = a.cav[r.cav];
-  int ii, jj;
-  bool wall;
-  double uwx, uwy;
-  wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx, uwy);
-  const int64_t b9 = 9 * cv.off;
-  const T *fb = (const T *)a.fb + b9;
+__device__ __forceinline__ void half_at(const StepArgs &a, const CavDev &cv, int ii, int jj,
+                                        T fh[9]) {
+  const T *fb = (const T *)a.fb + 9 * cv.off;
   const int64_t node = int64_t(jj) * cv.pitch + ii;
   const T lam = ((const T *)a.lam_out)[cv.off + node];
-
   const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
   const T hdt = T(0.5 * cv.dt);
   T fbar[9];
@@ -203,16 +197,75 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
   equilibrium(P, ux, uy, c, ics2, geq);
   const T L = T(lam), dt = T(cv.dt);
   const T bh = dt / (T(4) * L + dt);             // Eq. (2.17): 4 lam/(4 lam + dt) = 1 - bh
-  T fh[9];
 #pragma unroll
   for (int q = 0; q < 9; ++q) fh[q] = toward(fbar[q], geq[q], bh);
-  if (wall) nee(fh, T(uwx), GEN ? T(uwy) : T(0), cv);
-  store9((T *)a.fh + b9, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
+}
+
+// Pressure of a deviation set (Eq. 2.11).
+template <class T>
+__device__ __forceinline__ T pressure_of(const T g[9], const CavDev &cv) {
+  T ux, uy, P;
+  moments(g, T(cv.c), T(cv.cs2), ux, uy, P);
+  return P;
+}
+
+// Wall value from the inner neighbour's F (in F on entry). Zeroth-order wall
+// pressure: P_b = P_nb. First order (cv.wallp): P_b = 2 P_nb - P_nnb with
+// F2 the same quantity at the next node beyond the neighbour.
+template <class T>
+__device__ __forceinline__ void wall_rule(T F[9], const T F2[9], bool first, double uwx,
+                                          double uwy, const CavDev &cv) {
+  if (!first) {
+    nee(F, T(uwx), T(uwy), cv);
+    return;
+  }
+  const T Pb = T(2) * pressure_of(F, cv) - pressure_of(F2, cv);
+  nee_p(F, T(uwx), T(uwy), Pb, T(cv.c), T(cv.cs2), T(cv.inv_cs2));
+}
+
+template <class T, bool GEN>
+__global__ void __launch_bounds__(TILE_X *TILE_Y) k_half(StepArgs a) {
+  const NodeRef r = tile_node(a.tile_cav, a.cav);
+  if (!r.valid) return;
+  const CavDev &cv = a.cav[r.cav];
+  int ii, jj;
+  bool wall;
+  double uwx, uwy;
+  wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx, uwy);
+  T fh[9];
+  half_at<T, GEN>(a, cv, ii, jj, fh);
+  if (wall) {
+    T f2[9];
+    if (cv.wallp) half_at<T, GEN>(a, cv, 2 * ii - r.i, 2 * jj - r.j, f2);
+    wall_rule(fh, f2, cv.wallp != 0, uwx, GEN ? uwy : 0.0, cv);
+  }
+  store9((T *)a.fh + 9 * cv.off, cv.plane, int64_t(r.j) * cv.pitch + r.i, fh);
 }
 
 // ---------------------------------------------------------------------------
 // Steps (5)-(6): full step, wall nodes, residual partials
 // ---------------------------------------------------------------------------
+// f-hat(t + dt) at interior node (ii, jj): the full step of Eq. (3.6).
+template <class T, bool GEN>
+__device__ __forceinline__ void full_at(const StepArgs &a, const CavDev &cv, int ii, int jj,
+                                        T gn[9]) {
+  const int64_t b9 = 9 * cv.off;
+  const T *fh = (const T *)a.fh + b9;
+  const T *fp = (const T *)a.fp + b9;
+  const int64_t node = int64_t(jj) * cv.pitch + ii;
+  const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
+  const T dt = T(cv.dt);
+  gn[0] = fp[node];
+#pragma unroll
+  for (int q = 1; q < 9; ++q) {
+    const T *F = fh + q * cv.plane;
+    double cx, ce;
+    contravariant(met, q, cx, ce);
+    gn[q] = fp[q * cv.plane + node] -
+            dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, T(cx), T(ce), cv);  // Eq. (3.6)
+  }
+}
+
 template <class T, bool GEN>
 __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
   const NodeRef r = tile_node(a.tile_cav, a.cav);
@@ -224,22 +277,13 @@ __global__ void __launch_bounds__(TILE_X *TILE_Y) k_full(StepArgs a) {
     double uwx, uwy;
     wall_neighbour(cv, r.i, r.j, ii, jj, wall, uwx, uwy);
     const int64_t b9 = 9 * cv.off;
-    const T *fh = (const T *)a.fh + b9;
-    const T *fp = (const T *)a.fp + b9;
-    const int64_t node = int64_t(jj) * cv.pitch + ii;
-    const NodeMetrics<GEN> met = node_metrics<GEN>(cv, a.geo, ii, jj, node);
-    const T dt = T(cv.dt);
     T gn[9];
-    gn[0] = fp[node];
-#pragma unroll
-    for (int q = 1; q < 9; ++q) {
-      const T *F = fh + q * cv.plane;
-      double cx, ce;
-      contravariant(met, q, cx, ce);
-      gn[q] = fp[q * cv.plane + node] -
-              dt * advect(F, node, cv.pitch, ii, jj, cv.nx, cv.ny, T(cx), T(ce), cv);  // Eq. (3.6)
+    full_at<T, GEN>(a, cv, ii, jj, gn);
+    if (wall) {
+      T g2[9];
+      if (cv.wallp) full_at<T, GEN>(a, cv, 2 * ii - r.i, 2 * jj - r.j, g2);
+      wall_rule(gn, g2, cv.wallp != 0, uwx, GEN ? uwy : 0.0, cv);
     }
-    if (wall) nee(gn, T(uwx), GEN ? T(uwy) : T(0), cv);
     const int64_t me = int64_t(r.j) * cv.pitch + r.i;
     store9((T *)a.g_out + b9, cv.plane, me, gn);
 

@@ -19,7 +19,8 @@ _SCHED = {"grid": capi.IFDLBM_SCHED_GRID, "static": capi.IFDLBM_SCHED_STATIC,
 
 def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, dt=None,
                  gamma_min=None, graph_chunk=None, fused_threads=None, fused_rows=None,
-                 schedule=None, dt_mode=None, lambda_mode=None, power_fp32=None):
+                 schedule=None, dt_mode=None, lambda_mode=None, power_fp32=None,
+                 wall_pressure=None):
     opt = capi.ifdlbm_default_options()
     opt.precision = _PREC[precision]
     opt.kernel = _KERN[kernel]
@@ -35,6 +36,9 @@ def make_options(precision="fp64", kernel="auto", eta_b=None, cfl=None, c=None, 
                        "contravariant": capi.IFDLBM_DT_CONTRAVARIANT}[dt_mode]
     if power_fp32 is not None:
         opt.power_fp32 = int(bool(power_fp32))
+    if wall_pressure is not None:
+        opt.wall_pressure = {"zeroth": capi.IFDLBM_WALLP_ZEROTH,
+                             "first": capi.IFDLBM_WALLP_FIRST}[wall_pressure]
     if lambda_mode is not None:
         opt.lambda_mode = {"lagged": capi.IFDLBM_LAMBDA_LAGGED,
                            "implicit": capi.IFDLBM_LAMBDA_IMPLICIT}[lambda_mode]

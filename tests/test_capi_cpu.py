@@ -71,7 +71,7 @@ def test_invalid_arguments_rejected_before_device_use(lib, args, frag):
 def test_invalid_options_rejected(lib):
     from paper_2306_07603_gb300 import capi
     for field, val in (("eta_b", 1.5), ("cfl", 0.0), ("precision", 7), ("graph_chunk", 3),
-                       ("power_fp32", 1), ("power_fp32", 2)):
+                       ("power_fp32", 1), ("power_fp32", 2), ("wall_pressure", 2)):
         o = capi.ifdlbm_default_options()
         setattr(o, field, val)
         with pytest.raises(capi.IfdlbmError) as e:
@@ -87,6 +87,15 @@ def test_no_cpu_fallback_without_a_gpu(lib):
     with pytest.raises(capi.IfdlbmError) as e:
         capi.ifdlbm_create(9, 9, (1, 1, 60), 100, 0.75, 0.1)
     assert e.value.code == capi.IFDLBM_ERR_CUDA
+
+
+def test_first_order_wall_pressure_refuses_the_fused_kernel(lib):
+    from paper_2306_07603_gb300 import capi
+    o = capi.ifdlbm_default_options()
+    o.wall_pressure, o.kernel = capi.IFDLBM_WALLP_FIRST, capi.IFDLBM_KERNEL_FUSED
+    with pytest.raises(capi.IfdlbmError) as e:
+        capi.ifdlbm_create(9, 9, (1, 1, 60), 100, 0.75, 0.1, o)
+    assert e.value.code == capi.IFDLBM_ERR_INVALID_ARG and "staged" in str(e.value)
 
 
 def test_null_handle_calls_fail_cleanly(lib):

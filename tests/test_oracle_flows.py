@@ -190,3 +190,46 @@ def test_primary_eddy_centre_table2(golden_dir):
     x, y = run.g.x[j, i], run.g.y[j, i]
     h = 1.0 / 32
     assert abs(x - row[2]) < 1.5 * h * (1 + 2 / math.sqrt(3)) and abs(y - row[3]) < 1.5 * h
+
+
+@pytest.mark.parametrize("theta,corners", [(90.0, True), (60.0, False)])
+def test_wall_rule_first_order_pressure_is_exact_for_linear_pressure(theta, corners):
+    """The alternative wall reading (first-order pressure, P_b = 2 P_nb - P_nnb):
+    on an equilibrium state with a pressure linear in (x, y) and no flow, the
+    wall rule must give every wall node f^eq of the exact linear pressure
+    there (linear extrapolation along a grid line is exact for a linear
+    function of the line parameter). On the theta = 60 deg map the diagonal
+    corner lines are not straight in (x, y), so only the edges are checked
+    there. The zeroth-order reading (P_b = P_nb) misses by the pressure step."""
+    g = O.cavity_grid(9, 11, 1.0, 1.0, theta)
+    for side in g.wall_u:
+        nn = len(g.wall_u[side][0])
+        g.wall_u[side] = (np.zeros(nn), np.zeros(nn))
+    P = 1e-3 + 2e-3 * g.x - 3e-3 * g.y
+    F0 = O.equilibrium(P, 0.0 * P, 0.0 * P)
+    expect = O.equilibrium(P, 0.0 * P, 0.0 * P)
+    mask = np.zeros((g.ny, g.nx), dtype=bool)
+    mask[0, 1:-1] = mask[-1, 1:-1] = True
+    mask[1:-1, 0] = mask[1:-1, -1] = True
+    if corners:
+        mask[0, 0] = mask[0, -1] = mask[-1, 0] = mask[-1, -1] = True
+    for wp, exact in ((1, True), (0, False)):
+        prm = O.Params(dt=0.01, K=0.01, n=1.0, gamma_min=1e-4, eta_b=0.5, wall_pressure=wp)
+        F = O.nee_boundary(F0.copy(), g, prm)
+        err = np.abs(F - expect)[:, mask].max()
+        assert (err < 1e-14) == exact, (wp, err)
+
+
+def test_free_stream_preserved_with_first_order_wall_pressure():
+    g = O.cavity_grid(17, 15, 1.0, 1.0, 60.0)
+    u0, v0, p0 = 0.04, -0.03, 2e-3
+    for side in g.wall_u:
+        nn = len(g.wall_u[side][0])
+        g.wall_u[side] = (np.full(nn, u0), np.full(nn, v0))
+    prm = O.Params(dt=0.5 / 16, K=0.002, n=0.75, gamma_min=1e-4, eta_b=0.5, wall_pressure=1)
+    shape = (g.ny, g.nx)
+    fhat, lam = O.initial_state(g, prm, np.full(shape, p0), np.full(shape, u0), np.full(shape, v0))
+    f0 = fhat.copy()
+    for _ in range(100):
+        fhat, lam = O.step(fhat, lam, g, prm)
+    assert np.abs(fhat - f0).max() < 1e-14
