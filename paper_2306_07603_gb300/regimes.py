@@ -205,6 +205,10 @@ def main(argv=None):
     p.add_argument("--dt-mode", choices=["contravariant", "grid"], default=None,
                    help="time-step rule (default contravariant)")
     p.add_argument("--cfl", type=float, default=None, help="Courant number (default 0.5)")
+    p.add_argument("--wall-pressure", choices=["zeroth", "first"], default=None,
+                   help="pressure of the wall rule (default zeroth; first runs on the staged "
+                        "kernels)")
+    p.add_argument("--kernel", choices=["auto", "staged", "fused"], default=None)
     p.add_argument("--only", default=None,
                    help="with --cases: comma-separated indices of the cases to run")
     p.add_argument("--compare-precisions", action="store_true",
@@ -226,6 +230,10 @@ def main(argv=None):
         opts["dt_mode"] = a.dt_mode
     if a.cfl is not None:
         opts["cfl"] = a.cfl
+    if a.wall_pressure is not None:
+        opts["wall_pressure"] = a.wall_pressure
+    if a.kernel is not None:
+        opts["kernel"] = a.kernel
     if a.compare_precisions:
         rows, secs = compare_precisions(specs, a.transient, a.steps, a.every, **opts)
         print(json.dumps({"compare": "fp32dev vs fp64", "eta_b": opts.get("eta_b", 0.5),
@@ -238,6 +246,7 @@ def main(argv=None):
                             dt=np.array(rec["dt"]), every=a.every)
     print(json.dumps({"precision": a.precision, "eta_b": opts.get("eta_b", 0.5),
                       "dt_mode": opts.get("dt_mode", "contravariant"), "cfl": opts.get("cfl", 0.5),
+                      "wall_pressure": opts.get("wall_pressure", "zeroth"),
                       "transient": a.transient, "steps": a.steps,
                       "every": a.every, "seconds": round(rec["seconds"], 1),
                       "mlups": round(rec["lattice_updates"] / rec["seconds"] / 1e6, 1),

@@ -69,12 +69,14 @@ def _mean_fields(s, ncav, steps, every):
 
 
 def compare(workload="sweep257", tol=1e-8, max_steps=200000, chunk=2000, kernel="auto",
-            fp32_factor=3, window=0, every=1000):
+            fp32_factor=3, window=0, every=1000, only=None):
     """FP64 run to `tol` (or `max_steps`), then the FP32-deviation run (see the
     module docstring). With `window` > 0, the cavities whose FP64 run did not
     reach `tol` are also compared by their time-mean fields over the window of
     `window` steps that follows, sampled every `every` steps, in both forms."""
     specs = WORKLOADS[workload]()
+    if only:
+        specs = [specs[k] for k in only]
     opts = dict(WORKLOAD_OPTIONS.get(workload, {}), kernel=kernel)
     s = _solver(specs, "fp64", **opts)
     steps, t0 = 0, time.time()
@@ -135,9 +137,11 @@ def main(argv=None):
                    help="steps of the time-mean comparison of the cavities that do not settle")
     p.add_argument("--every", type=int, default=1000)
     p.add_argument("--save", default=None, help="also write the result to this JSON file")
+    p.add_argument("--only", default=None, help="comma-separated indices of the cavities to run")
     a = p.parse_args(argv)
+    only = [int(k) for k in a.only.split(",")] if a.only else None
     out = compare(a.workload, a.tol, a.max_steps, a.chunk, a.kernel, a.fp32_factor, a.window,
-                  a.every)
+                  a.every, only)
     if a.save:
         with open(a.save, "w") as f:
             json.dump(out, f, indent=1)
