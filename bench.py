@@ -53,6 +53,10 @@ ALGO_BYTES = {
 # FP64 metrics (xi_x, xi_y, eta_x, eta_y; k_full also J).
 ALGO_BYTES_GENERAL = {"half": 32, "full": 40}
 FALLBACK_HBM_GBS = 6800.0
+# GB300 instruction issue: 152 SMs x 4 schedulers, one warp instruction per clock each,
+# at the maximum SM clock (MHz)
+ISSUE_SLOTS_PER_CLOCK = 152 * 4
+SM_MAX_MHZ = 2070.0
 
 
 def parse_args(argv=None):
@@ -535,6 +539,18 @@ def run_ours(args):
         issue = {"bound": "issue", "unit": "fraction of cycles the SM schedulers issue",
                  "frac": round(rec["issue_active_pct"] / 100.0, 3),
                  "source": rec["source"] + " (ncu smsp__issue_active, active cycles)"}
+        if "warp_inst_per_node" in rec and dom is not None:
+            # the same bound from this run's own timing: warp instructions per node (ncu,
+            # same kernel sources) x nodes per launch / launch time, against the issue
+            # peak of 152 SMs x 4 schedulers x 1 instruction per clock at the max clock
+            ms, n = kern[dom]
+            rate = rec["warp_inst_per_node"] * lu_step / (ms / n * 1e-3) / 1e9
+            peak_issue = ISSUE_SLOTS_PER_CLOCK * SM_MAX_MHZ * 1e6 / 1e9
+            issue.update({"achieved": round(rate, 1), "peak": round(peak_issue, 1),
+                          "unit": "G warp instructions/s",
+                          "frac": round(rate / peak_issue, 4),
+                          "issue_active_ncu": round(rec["issue_active_pct"] / 100.0, 3),
+                          "warp_inst_per_node": rec["warp_inst_per_node"]})
     layout = fixed or (tuning_options(tuning) if tuning is not None else {})
     e2e = None
     if not args.no_e2e:
