@@ -50,8 +50,9 @@ ALGO_BYTES = {
     ("full", "fp32dev"): 132, ("full", "fp64"): 240,
 }
 # General quadrilaterals: the staged stencil kernels also read the per-node
-# FP64 metrics (xi_x, xi_y, eta_x, eta_y; k_full also J).
-ALGO_BYTES_GENERAL = {"half": 32, "full": 40}
+# FP64 metrics (xi_x, xi_y, eta_x, eta_y; k_full also J); the fused FP32 kernel
+# their FP32 roundings (c xi_x, c xi_y, c eta_x, c eta_y, J).
+ALGO_BYTES_GENERAL = {"half": 32, "full": 40, "fused": 20}
 FALLBACK_HBM_GBS = 6800.0
 # GB300 instruction issue: 152 SMs x 4 schedulers, one warp instruction per clock each,
 # at the maximum SM clock (MHz)
@@ -360,8 +361,9 @@ def cpu_baseline(specs, seconds):
     mlups, n, dt, _ = oracle_sample_mlups(spec, seconds)
     cores = host_cores()
     workers = min(cores, len(specs))
-    per_group = -(-len(specs) // workers)                 # cavities per process
-    steps = max(2, int(seconds / (per_group * dt / n)))
+    # steps for about `seconds` of the largest process group at the sampled rate
+    group_nodes = max(sum(sp.nodes for sp in specs[k::workers]) for k in range(workers))
+    steps = max(2, int(seconds * mlups * 1e6 / group_nodes))
     pool, wall, used = oracle_pool_mlups(specs, 1, steps, workers)
     return {"value": round(pool, 4), "unit": "MLUPS", "cores": used, "kind": "oracle",
             "sample": f"FP64 NumPy oracle, all {len(specs)} cavities of the workload from rest, "

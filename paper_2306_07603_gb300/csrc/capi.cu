@@ -775,11 +775,11 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   ok &= (h->b.cav_done = (int *)A(size_t(ncav) * sizeof(int))) != nullptr;
   ok &= (h->b.ptile = (double *)A(size_t(h->ntiles + ncav) * sizeof(double))) != nullptr;
   double *gmet = nullptr;
-  float *qsep = nullptr;  // x_xi, y_xi, x_eta, y_eta of the bilinear maps (fused FP32 kernel)
+  float *qmet_f = nullptr;  // FP32 roundings of the FP64 metrics (fused FP32 kernel)
   double *qcorners = nullptr;
   if (quads) ok &= (gmet = (double *)A(size_t(7 * off) * sizeof(double))) != nullptr;
   if (quads) ok &= (qcorners = (double *)A(size_t(8 * ncav) * sizeof(double))) != nullptr;
-  if (quads) ok &= (qsep = (float *)A(size_t(4 * goff) * sizeof(float))) != nullptr;
+  if (quads && fused) ok &= (qmet_f = (float *)A(size_t(5 * off) * sizeof(float))) != nullptr;
   if (!ok) {
     release_all(h);
     delete h;
@@ -792,25 +792,8 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   h->b.geo.cxix_f = geof;
   h->b.geo.jac_f = geof + goff;
   h->b.geo.gmet = gmet;
-  h->b.geo.qxxi_f = qsep;
-  h->b.geo.qyxi_f = qsep ? qsep + goff : nullptr;
-  h->b.geo.qxeta_f = qsep ? qsep + 2 * goff : nullptr;
-  h->b.geo.qyeta_f = qsep ? qsep + 3 * goff : nullptr;
-  std::vector<float> qsep_h(quads ? 4 * goff : 0);
-  for (int k = 0; quads && k < ncav; ++k) {
-    const CavDev &cv = h->cav[k];
-    const double *cr = quads[k].corners;
-    for (int j = 0; j < cv.ny; ++j) {
-      const double eta = double(j) / (cv.ny - 1);
-      qsep_h[cv.goff + j] = float((1 - eta) * (cr[2] - cr[0]) + eta * (cr[6] - cr[4]));
-      qsep_h[goff + cv.goff + j] = float((1 - eta) * (cr[3] - cr[1]) + eta * (cr[7] - cr[5]));
-    }
-    for (int i = 0; i < cv.nx; ++i) {
-      const double xi = double(i) / (cv.nx - 1);
-      qsep_h[2 * goff + cv.goff + i] = float((1 - xi) * (cr[4] - cr[0]) + xi * (cr[6] - cr[2]));
-      qsep_h[3 * goff + cv.goff + i] = float((1 - xi) * (cr[5] - cr[1]) + xi * (cr[7] - cr[3]));
-    }
-  }  std::vector<float> geof_h(2 * goff);
+  h->b.geo.qmet_f = qmet_f;
+  std::vector<float> geof_h(2 * goff);
   for (int k = 0; k < ncav; ++k) {
     const CavDev &cv = h->cav[k];
     for (int j = 0; j < cv.ny; ++j) {
@@ -831,7 +814,7 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   cudaStream_t s = h->stream;
   h->h2d_bytes = int64_t(tile_cav.size() * sizeof(int) + h->cav.size() * sizeof(CavDev) +
                          geo_h.size() * sizeof(double) + geof_h.size() * sizeof(float) +
-                         ifd::POW_TABLE_SIZE * sizeof(double) + qsep_h.size() * sizeof(float) +
+                         ifd::POW_TABLE_SIZE * sizeof(double) +
                          size_t(ncav) * ifd::POWT_SIZE * sizeof(double) +
                          (quads ? size_t(8 * ncav) * sizeof(double) : 0));
   e = cudaMemcpyAsync(h->b.tile_cav, tile_cav.data(), tile_cav.size() * sizeof(int),
@@ -858,9 +841,14 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
       e = cudaGetLastError();
     }
   }
-  if (qsep && e == cudaSuccess)
-    e = cudaMemcpyAsync(qsep, qsep_h.data(), qsep_h.size() * sizeof(float),
-                        cudaMemcpyHostToDevice, s);
+  if (qmet_f && e == cudaSuccess) {
+    e = cudaMemsetAsync(qmet_f, 0, size_t(5 * off) * sizeof(float), s);  // row padding too
+    if (e == cudaSuccess) {
+      ifd::launch_quad_metrics_f32(h->b.cav, ncav, h->max_n2, gmet, qmet_f, s);
+      g_launches += 1;
+      e = cudaGetLastError();
+    }
+  }
   static std::vector<double> powtab_h = [] {
     std::vector<double> t(ifd::POW_TABLE_SIZE);
     ifd::fill_pow_tables(t.data());

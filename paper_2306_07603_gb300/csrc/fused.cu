@@ -275,12 +275,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const T Es1 = T(0.5 * cv.dt * cv.inv2deta * cv.c / cv.H), Es2 = T(cv.dt * cv.inv2deta * cv.c / cv.H);
   const T ku = T(1.0 - cv.eta_b), ku3 = T(3.0 * (1.0 - cv.eta_b));
   const T xeH = GEN ? T(0) : T(a.geo.xeH[goff + cc]);  // x_eta / H of this column
-  // general quadrilateral (bilinear map): x_eta, y_eta of this column and
-  // x_xi, y_xi of a row; the node's metrics follow from Eqs. (3.2)-(3.3)
-  const T gxe = GEN ? T(a.geo.qxeta_f[goff + cc]) : T(0);
-  const T gye = GEN ? T(a.geo.qyeta_f[goff + cc]) : T(0);
-  auto row_xxi = [&](int j) -> T { return a.geo.qxxi_f[goff + j]; };
-  auto row_yxi = [&](int j) -> T { return a.geo.qyxi_f[goff + j]; };
+  // general quadrilateral: the node's c xi_x, c xi_y, c eta_x, c eta_y and J of
+  // Eqs. (3.2)-(3.3), formed in FP64 at creation and rounded to FP32 planes
+  const float *qm = GEN ? a.geo.qmet_f + 5 * cv.off : nullptr;
+  auto qmet = [&](int k, int j) -> T { return qm[k * plane + int64_t(j) * pitch + cc]; };
   const T wx = T(((c == 0 || c == nx - 1) ? 0.5 : 1.0) * cv.dxi);
   const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
@@ -452,10 +450,9 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         const T *cols[5] = {&S.fb[slot6(m - 2)][0][l], &S.fb[slot6(m - 1)][0][l], &S.fb[sm][0][l],
                             &S.fb[slot6(m + 1)][0][l], &S.fb[slot6(m + 2)][0][l]};
         if constexpr (GEN) {
-          const T X = row_xxi(m), Y = row_yxi(m);
-          const T iJ = c_ / (X * gye - gxe * Y);         // c / J of node (c, m)
-          AdvectAllGen<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
-                                          iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, hdt,
+          AdvectAllGen<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, qmet(0, m), qmet(1, m),
+                                          qmet(2, m), qmet(3, m), clo, chi, lo, hi, eta_b, i2dxi,
+                                          i2deta, hdt,
                                           &S.fb[sm][0][l], fbar);  // Eq. (3.7)
         } else {
           const T As = A1 * hxs;                         // dt/2 c xi_x / (2 dxi) of row m
@@ -514,10 +511,9 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         const T *cols[5] = {&S.fh[slot6(o - 2)][0][l], &S.fh[slot6(o - 1)][0][l], &S.fh[so][0][l],
                             &S.fh[slot6(o + 1)][0][l], &S.fh[slot6(o + 2)][0][l]};
         if constexpr (GEN) {
-          const T X = row_xxi(o), Y = row_yxi(o);
-          const T iJ = c_ / (X * gye - gxe * Y);         // c / J of node (c, o)
-          AdvectAllGen<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, iJ * gye, -iJ * gxe, -iJ * Y,
-                                          iJ * X, clo, chi, lo, hi, eta_b, i2dxi, i2deta, dt,
+          AdvectAllGen<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, qmet(0, o), qmet(1, o),
+                                          qmet(2, o), qmet(3, o), clo, chi, lo, hi, eta_b, i2dxi,
+                                          i2deta, dt,
                                           sfme + sp * SLOT, gnv);  // Eq. (3.6)
         } else {
           const T As = A2 * fxs;                         // dt c xi_x / (2 dxi) of row o
@@ -560,7 +556,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         moments(fpo, c_, cs2, u0, v0, P0);  // u, P at t (moments of f-hat^+ equal those of f-hat)
         T Jo;
         if constexpr (GEN)
-          Jo = row_xxi(o) * gye - gxe * row_yxi(o);    // Jacobian of node (c, o)
+          Jo = qmet(4, o);                             // Jacobian of node (c, o)
         else
           Jo = J2o;
         const T wJ = wx * wy_in * Jo;
@@ -590,7 +586,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
           const int e = bottom ? 0 : 1;
           T Jr;
           if constexpr (GEN)
-            Jr = row_xxi(r) * gye - gxe * row_yxi(r);
+            Jr = qmet(4, r);
           else
             Jr = row_jac(r);
           const T wJ = wx * wy_edge * Jr;

@@ -55,10 +55,11 @@ struct Geo {
   // general quadrilaterals (staged kernels): per node, at 7 * off + k * plane,
   // k = 0..6: xi_x, xi_y, eta_x, eta_y, x_eta, y_eta, J (Eqs. 3.2-3.3)
   const double *gmet;
-  // general quadrilaterals (fused FP32 kernel): the bilinear map's separable
-  // derivatives as floats, at goff: x_xi(eta_j), y_xi(eta_j) (ny entries),
-  // x_eta(xi_i), y_eta(xi_i) (nx entries)
-  const float *qxxi_f, *qyxi_f, *qxeta_f, *qyeta_f;
+  // general quadrilaterals (fused FP32 kernel): per node, at 5 * off + k * plane,
+  // k = 0..4: c xi_x, c xi_y, c eta_x, c eta_y, J, each the FP32 rounding of
+  // the FP64 value of gmet (the metrics are formed in FP64; only the FP32
+  // arithmetic that uses them sees them rounded)
+  const float *qmet_f;
 };
 
 // Device buffers of a handle. T is double (FP64) or float (FP32DEV).
@@ -199,6 +200,9 @@ __host__ __device__ inline void quad_node_metrics(const double *cr, double xi, d
 // handle, from corners [ncav][8]; max_n2 = the largest nx * ny.
 void launch_quad_metrics(const CavDev *cav, int ncav, int64_t max_n2, const double *corners,
                          double *gmet, cudaStream_t s);
+// The float planes Geo::qmet_f of the fused FP32 kernel, from the FP64 planes gmet.
+void launch_quad_metrics_f32(const CavDev *cav, int ncav, int64_t max_n2, const double *gmet,
+                             float *qmet_f, cudaStream_t s);
 void launch_pow_selftest(int n, const double *x, double m, const double *tab, double *fast,
                          double *ref, cudaStream_t s);
 

@@ -570,6 +570,27 @@ __global__ void k_quad_metrics(const CavDev *cavs, const double *corners, double
   for (int t = 0; t < 7; ++t) gm[t * cv.plane + node] = m[t];
 }
 
+// FP32 roundings of c xi_x, c xi_y, c eta_x, c eta_y and J (formed in FP64 by
+// k_quad_metrics), one thread per node (blockIdx.y = cavity).
+__global__ void k_quad_metrics_f32(const CavDev *cavs, const double *gmet, float *qmet_f) {
+  const CavDev &cv = cavs[blockIdx.y];
+  const int64_t n = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (n >= int64_t(cv.nx) * cv.ny) return;
+  const int j = int(n / cv.nx), i = int(n - int64_t(j) * cv.nx);
+  const int64_t node = int64_t(j) * cv.pitch + i;
+  const double *gm = gmet + 7 * cv.off;
+  float *qm = qmet_f + 5 * cv.off;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) qm[t * cv.plane + node] = float(cv.c * gm[t * cv.plane + node]);
+  qm[4 * cv.plane + node] = float(gm[6 * cv.plane + node]);
+}
+
+void launch_quad_metrics_f32(const CavDev *cav, int ncav, int64_t max_n2, const double *gmet,
+                             float *qmet_f, cudaStream_t s) {
+  const dim3 grid(unsigned((max_n2 + 255) / 256), unsigned(ncav));
+  k_quad_metrics_f32<<<grid, 256, 0, s>>>(cav, gmet, qmet_f);
+}
+
 void launch_quad_metrics(const CavDev *cav, int ncav, int64_t max_n2, const double *corners,
                          double *gmet, cudaStream_t s) {
   const dim3 grid(unsigned((max_n2 + 255) / 256), unsigned(ncav));
