@@ -451,6 +451,15 @@ int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes
 int ifdlbm_selftest_pow(ifdlbm_handle h, int n, const double *x, double m, double *fast,
                         double *ref);
 
+/* Test hook of the fused kernel's failure path (no counterpart in the paper).
+ * While `enable` is nonzero the fused kernel issues no TMA row loads, so that
+ * every bounded wait for one runs out (after about a second per warp); the
+ * kernel records that in the status word, which the next synchronising call
+ * reports as IFDLBM_ERR_TIMEOUT. The state computed meanwhile is meaningless;
+ * the device context stays usable. Synchronises; drops captured graphs.
+ * Errors: INVALID_ARG for a NULL handle or one on the staged kernels. */
+int ifdlbm_inject_tma_timeout(ifdlbm_handle h, int enable);
+
 /* Self-test of the FP64 power the FP32-deviation form uses for Eq. (1.4)
  * (FP32 strain rate, FP64 result): for n DEVICE doubles x[k] whose float
  * roundings xf_k are normal and > 0, writes out[k] = C xf_k^m as the library

@@ -130,6 +130,7 @@ _SIGS = {
     "ifdlbm_selftest_pow": (C.c_int, [_H, C.c_int, _P, C.c_double, _P, _P]),
     "ifdlbm_selftest_pow_f32": (C.c_int, [_H, C.c_int, _P, C.c_double, _P]),
     "ifdlbm_selftest_pow_tab": (C.c_int, [_H, C.c_int, C.c_int, _P, _P]),
+    "ifdlbm_inject_tma_timeout": (C.c_int, [_H, C.c_int]),
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
@@ -404,6 +405,10 @@ def ifdlbm_selftest_pow_tab(h, cavity, x, out):
     _device_f64("x", x, n)
     _device_f64("out", out, 2 * n)
     return _check(load_library().ifdlbm_selftest_pow_tab(h, int(cavity), n, _ptr(x), _ptr(out)), h)
+
+
+def ifdlbm_inject_tma_timeout(h, enable=True):
+    return _check(load_library().ifdlbm_inject_tma_timeout(h, int(bool(enable))), h)
 
 
 def ifdlbm_selftest_pow_f32(h, x, m, out):

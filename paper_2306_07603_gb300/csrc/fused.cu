@@ -300,19 +300,28 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   T *const sfme = &S.sf[0][wid][0][lane];               // this thread's column of slot 0
   const int tx = i0 - 4 + (l & ~31);
   const void *tmap = static_cast<const char *>(a.tmap_in) + size_t(task.cav) * TMAP_BYTES;
+  const bool aligned = (tx & 3) == 0;
+  const bool issue = aligned && !a.tma_skip;
   auto prefetch = [&](int it) {
     const int r = row_of(it);
-    if (lane == 0 && r >= rlo && r <= rhi && (tx & 3) == 0)
+    if (lane == 0 && r >= rlo && r <= rhi && issue)
       tma_load_box3(&S.sf[it % PF][wid][0][0], tmap, tx, r, &S.bar[it % PF][wid],
                     uint32_t(9 * 32 * sizeof(T)));
   };
+  // A wait that runs out is reported in the status word; the warp then waits
+  // no more for rows in this task (their data are lost anyway), so that a
+  // failing task ends after one bounded wait per warp, and the end of the task
+  // waits, bounded too, for the last copy it issued into each slot. The phase
+  // bits follow the issued copies only.
+  bool gave_up = false;
   auto wait_row = [&](int it) {
     const int r = row_of(it);
     if (r >= rlo && r <= rhi) {
       const int s = it % PF;
-      const bool ok = (tx & 3) == 0 && mbar_wait(&S.bar[s][wid], (phase >> s) & 1u);
-      if (!ok && lane == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
-      if ((tx & 3) == 0) phase ^= 1u << s;
+      const bool ok = aligned && !gave_up && mbar_wait(&S.bar[s][wid], (phase >> s) & 1u);
+      if (!ok && !gave_up && lane == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
+      gave_up = gave_up || !ok;
+      if (issue) phase ^= 1u << s;
     }
   };
   // lambda_prev of a row Step (2) works on, loaded one iteration ahead
@@ -599,6 +608,11 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     // the TMA copies that refill them after the next barrier
     fence_proxy_async_smem();
   }
+  // After a wait ran out, wait (bounded) for the last copy issued into each
+  // slot, so that none is left writing into shared memory the next task uses
+  // (a slot's previous phase counts as complete when none was issued).
+  if (gave_up && issue)
+    for (int s = 0; s < PF; ++s) mbar_wait(&S.bar[s][wid], ((phase >> s) & 1u) ^ 1u);
   if (a.want_residual) {
     leaf_flush(leaf, p);
     p.du2max = double(leaf.du2max);

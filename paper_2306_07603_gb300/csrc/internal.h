@@ -132,6 +132,7 @@ struct FusedArgs {
   int implicit;        // 1: implicit form of Eq. (2.14) (kernel variant), 0: lagged
   int general;         // 1: general quadrilaterals (kernel variant; FP32, lagged)
   int pow32;           // 1: FP32 power law (opt-in of the FP32 form; kernel variant)
+  int tma_skip;        // test hook: 1 issues no TMA row loads, so that every row wait runs out
   double *resid;       // [ncav][4] residual outputs (formed by each cavity's last task)
   int want_residual;
 };
