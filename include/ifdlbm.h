@@ -403,7 +403,7 @@ int ifdlbm_residual_fields_static(int nx, int ny, const double *u1, const double
 
 /* Autotuner of the batched fused step (pattern "batching"): times
  * `trial_steps` >= 1 steps of every combination of fused_threads {64, 128,
- * 256}, rows per task {16, 32, 64, 128} and schedule {GRID,
+ * 256}, rows per task {16, 32, 64, 128, 256} and schedule {GRID,
  * STATIC, DYNAMIC} on the handle's own cavities, starting each trial from
  * the same saved state, and keeps the fastest. The state is restored
  * afterwards, so the call does not advance the simulation. Needs a handle

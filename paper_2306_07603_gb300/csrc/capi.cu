@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda.h>  // CUtensorMap and its encoder's types (the encoder is found at run time)
@@ -859,10 +860,24 @@ int create_impl(int ncav, const ifdlbm_cavity *cavs, const ifdlbm_quad_cavity *q
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->b.powtab, powtab_h.data(), powtab_h.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s);
+  // The per-cavity tables of pow_tab in extended precision: ~0.5 ms a cavity where
+  // long double is software quad precision, so the cavities are spread over host threads.
   std::vector<double> powt_h(size_t(ncav) * ifd::POWT_SIZE);
-  for (int k = 0; k < ncav; ++k)
-    ifd::fill_cavity_pow_table(powt_h.data() + size_t(k) * ifd::POWT_SIZE, h->cav[k].half_nm1,
-                               h->cav[k].Kics2);
+  {
+    auto fill = [&](int k0, int k1) {
+      for (int k = k0; k < k1; ++k)
+        ifd::fill_cavity_pow_table(powt_h.data() + size_t(k) * ifd::POWT_SIZE, h->cav[k].half_nm1,
+                                   h->cav[k].Kics2);
+    };
+    const int nth = std::max(1, std::min({ncav, 16, int(std::thread::hardware_concurrency())}));
+    if (nth == 1) {
+      fill(0, ncav);
+    } else {
+      std::vector<std::thread> pool;
+      for (int t = 0; t < nth; ++t) pool.emplace_back(fill, ncav * t / nth, ncav * (t + 1) / nth);
+      for (auto &th : pool) th.join();
+    }
+  }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->b.powt, powt_h.data(), powt_h.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s);
@@ -1393,7 +1408,7 @@ int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best) {
   ifdlbm_tuning b{};
   b.ms_per_step = 1e300;
   const int nts[3] = {64, 128, 256};
-  const int rows[4] = {16, 32, 64, 128};
+  const int rows[5] = {16, 32, 64, 128, 256};
   for (int nt : nts) {
     for (int r : rows)
       for (int sc = IFDLBM_SCHED_GRID; sc <= IFDLBM_SCHED_DYNAMIC; ++sc) {

@@ -21,16 +21,18 @@
 // place, its f-hat^+ until the full step two iterations later. The prefetch is
 // one TMA copy per warp (tma.cuh): a 3-D tiled bulk copy of the warp's 32
 // columns x 9 planes of the row into the warp's slot, completed on that slot's
-// mbarrier, so that no thread issues per-population loads. That is ~410 B per
-// thread in FP32, so that 16 warps fit on an SM. Four barriers per iteration
-// (two per row) order the stages across the halves.
+// mbarrier, so that no thread issues per-population loads. That is ~430 B per
+// thread in FP32, so that 16 warps fit on an SM. Three barriers per iteration
+// order the stages across the halves.
 //
 // Wall nodes follow the rule of the staged kernels: a side-wall node takes
 // its inner neighbour on the same row, a bottom/lid node the node
-// (clamp(i, 1, nx-2), 1 or ny-2); row 0 of f(t+dt/2) is made with row 1 and
-// row ny-1 at the position of the march where it would be computed. The
-// full-step values of columns 1 and nx-2, which the wall columns extrapolate
-// from, are published through a small shared array.
+// (clamp(i, 1, nx-2), 1 or ny-2). The wall nodes of f(t+dt/2) are written by
+// the thread that forms their neighbour in the half step (row 0 with row 1,
+// the side walls with columns 1 and nx-2, the lid row ny-1, which has a
+// buffer of its own, with row ny-2). The full-step values of columns 1 and
+// nx-2, which the wall columns of f-hat(t+dt) extrapolate from, are published
+// through a small shared array.
 //
 // FP64 work per node is kept to the power of Eq. (1.4) and the residual
 // accumulation: GB300 issues FP64 at 1/64 of the FP32 rate. With the pow32
@@ -61,6 +63,8 @@ struct FusedSmem {
   T fh[RING][9][NC];      // f(t + dt/2)
   T edge[2][3][NC];       // u, v, P(t) of rows 0 and ny-1 (wall-row residuals)
   T gw[2][2][9];          // f-hat(t+dt) of columns 1 and nx-2, per half
+  T lid[9][NC];           // f(t + dt/2) of the lid row ny-1 (written with row ny-2, which
+                          // can come one iteration before the ring slot of row ny-1 is free)
   uint64_t bar[PF][NW];   // mbarriers of the TMA row loads
 };
 // dynamic shared memory: the struct plus the slack of aligning it to 128 bytes
@@ -255,7 +259,6 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const bool own = colv && c >= i0 && c < i1;        // output column (i1 - i0 <= NC - 8)
   const bool inner_c = c >= 1 && c <= nx - 2;
   const bool wall_c = c == 0 || c == nx - 1;
-  const int ln = l + (min(max(c, 1), nx - 2) - c);   // lane of the inner neighbour column
   const bool clo = c == 1, chi = c == nx - 2;
 
   const int64_t b9 = 9 * cv.off;
@@ -476,35 +479,39 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       equilibrium(P, ux, uy, c_, ics2, geq);
       const T L = Lprev;                                 // lambda(t) of row m
       const T bh = dt / (T(4) * L + dt);                 // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
+      T fh[9];
 #pragma unroll
-      for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = toward(fbar[q], geq[q], bh);
+      for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = fh[q] = toward(fbar[q], geq[q], bh);
+      // Wall nodes of f(t + dt/2) that take this node as their neighbour, written
+      // by this thread: the side wall of its row (column 1 -> 0, nx-2 -> nx-1),
+      // the bottom (row 1 -> 0) and the lid (row ny-2 -> ny-1), and at the
+      // corners the diagonal wall node. Every one of them but the lid's moving
+      // nodes takes nee(F, 0); the lid's interior nodes take nee(F, u_lid).
+      if (clo || chi || lo || hi) {
+        T W[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) W[q] = fh[q];
+        nee(W, T(0), T(0), c_, cs2, ics2);
+        const int lw = clo ? l - 1 : l + 1;               // lane of the side wall column
+        const bool side = (clo || chi) && lw >= 2 && lw < NC - 2;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          if (side) S.fh[sm][q][lw] = W[q];                           // (m, 0) / (m, nx-1)
+          if (lo) S.fh[slot6(0)][q][l] = W[q];                        // (0, c)
+          if (side && lo) S.fh[slot6(0)][q][lw] = W[q];               // corner (0, 0) / (0, nx-1)
+          if (side && hi) S.lid[q][lw] = W[q];                        // corner (ny-1, 0) / (ny-1, nx-1)
+        }
+        if (hi) {                                                     // (ny-1, c): the lid
+#pragma unroll
+          for (int q = 0; q < 9; ++q) W[q] = fh[q];
+          nee(W, Uw, Uwy, c_, cs2, ics2);
+#pragma unroll
+          for (int q = 0; q < 9; ++q) S.lid[q][l] = W[q];
+        }
+      }
     }
     Lprev = Lcur;
-    __syncthreads();  // f(t + dt/2) of rows m
-
-    // ---------------- walls of f(t + dt/2) ----------------
-    if (l >= 2 && l < NC - 2 && colv) {
-      if (do1 && wall_c) {                            // side walls of row m
-        T F[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) F[q] = S.fh[slot6(m)][q][ln];
-        nee(F, T(0), T(0), c_, cs2, ics2);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) S.fh[slot6(m)][q][l] = F[q];
-      }
-      const bool bottom = m == 1 && do1;
-      const bool lid = m == ny - 1 && mhi == ny - 2 && mlo <= ny - 2;
-      if (bottom || lid) {                            // row 0 from row 1, row ny-1 from ny-2
-        const int src = lid ? slot6(ny - 2) : slot6(1), dst = lid ? slot6(ny - 1) : slot6(0);
-        T F[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) F[q] = S.fh[src][q][ln];
-        nee(F, (lid && inner_c) ? Uw : T(0), (lid && inner_c) ? Uwy : T(0), c_, cs2, ics2);
-#pragma unroll
-        for (int q = 0; q < 9; ++q) S.fh[dst][q][l] = F[q];
-      }
-    }
-    __syncthreads();  // wall values of f(t + dt/2)
+    __syncthreads();  // f(t + dt/2) of rows m, wall nodes included
 
     // ---------------- stage 2: row o = k - 4 + h ----------------
     const int o = k - 4 + h;
@@ -517,8 +524,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       const bool lo = o == 1, hi = o == ny - 2;
       gnv[0] = sfme[sp * SLOT];
       {
-        const T *cols[5] = {&S.fh[slot6(o - 2)][0][l], &S.fh[slot6(o - 1)][0][l], &S.fh[so][0][l],
-                            &S.fh[slot6(o + 1)][0][l], &S.fh[slot6(o + 2)][0][l]};
+        // rows o-2..o+2 of f(t + dt/2); the lid row ny-1 has a buffer of its own
+        auto fhrow = [&](int r) -> const T * {
+          return r == ny - 1 ? &S.lid[0][l] : &S.fh[slot6(r)][0][l];
+        };
+        const T *cols[5] = {fhrow(o - 2), fhrow(o - 1), &S.fh[so][0][l], fhrow(o + 1),
+                            fhrow(o + 2)};
         if constexpr (GEN) {
           AdvectAllGen<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, qmet(0, o), qmet(1, o),
                                           qmet(2, o), qmet(3, o), clo, chi, lo, hi, eta_b, i2dxi,

@@ -305,7 +305,7 @@ def test_autotune_keeps_state_and_result():
         runs.append(r)
     before = [s.get_state(k) for k in range(2)]
     t = s.autotune(trial_steps=2)
-    assert t.candidates == 36 and t.fused_threads in (64, 128, 256) and t.schedule in (0, 1, 2)
+    assert t.candidates == 45 and t.fused_threads in (64, 128, 256) and t.schedule in (0, 1, 2)
     info = s.info(0)
     assert (info.fused_threads, info.fused_rows, info.schedule) == (t.fused_threads, t.fused_rows,
                                                                      t.schedule)
