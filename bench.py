@@ -21,6 +21,7 @@ the value is all ranks' lattice updates over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import atexit
 import hashlib
 import json
 import os
@@ -128,8 +129,17 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={CLOCK_FIELDS}",
                  "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
                 stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            # ended on every exit path, an exception included: a sampler left
+            # running would outlive the bench (and keep a profiler that waits
+            # for the whole process tree waiting)
+            atexit.register(self._reap)
         except Exception:
             self.proc = None
+
+    def _reap(self):
+        if self.proc is not None and self.proc.poll() is None:
+            self.proc.kill()
+            self.proc.wait()
 
     def mark(self):
         self.marks.append(time.time())

@@ -27,12 +27,15 @@
 //
 // Wall nodes follow the rule of the staged kernels: a side-wall node takes
 // its inner neighbour on the same row, a bottom/lid node the node
-// (clamp(i, 1, nx-2), 1 or ny-2). The wall nodes of f(t+dt/2) are written by
-// the thread that forms their neighbour in the half step (row 0 with row 1,
-// the side walls with columns 1 and nx-2, the lid row ny-1, which has a
+// (clamp(i, 1, nx-2), 1 or ny-2). The wall nodes of f(t+dt/2) are written
+// by the thread that forms their neighbour in the half step (row 0 with row
+// 1, the side walls with columns 1 and nx-2, the lid row ny-1, which has a
 // buffer of its own, with row ny-2). The full-step values of columns 1 and
 // nx-2, which the wall columns of f-hat(t+dt) extrapolate from, are published
-// through a small shared array.
+// through a small shared array. In FP32 the first-order near-wall
+// differences of the stencils come from ghost values beyond the walls
+// (write_ghosts), written by the node that reads them, instead of per-plane
+// selects on the wall flags.
 //
 // FP64 work per node is kept to the power of Eq. (1.4) and the residual
 // accumulation: GB300 issues FP64 at 1/64 of the FP32 rate. With the pow32
@@ -73,7 +76,24 @@ constexpr int fused_smem_size() {
   return int(sizeof(FusedSmem<T, NT>)) + 128;
 }
 
-__device__ __forceinline__ int slot6(int r) { return (r + 12) % RING; }
+// Ring slot of row r (r >= -12) and prefetch slot of iteration it (it >= 0):
+// unsigned remainders by constants, a multiply-high and a shift each.
+__device__ __forceinline__ int slot6(int r) { return int(unsigned(r + 12) % unsigned(RING)); }
+__device__ __forceinline__ int pf_slot(int it) { return int(unsigned(it) % unsigned(PF)); }
+
+// a / b for the relaxation weights and the strain-rate factor, whose
+// denominators (2 lam + dt, 4 lam + dt, (2 lam + dt) c_s^2) are positive and
+// normal: a division in FP64; in FP32 the hardware reciprocal approximation
+// (__fdividef, within 2 ulp). The transforms of Eqs. (2.15)-(2.17) move F
+// towards f^eq, so an error in their weights leaves u and P unchanged and
+// reaches the populations at 2e-7 of |f^eq - F|.
+template <class T>
+__device__ __forceinline__ T quot(T a, T b) {
+  if constexpr (sizeof(T) == 4)
+    return __fdividef(a, b);
+  else
+    return a / b;
+}
 
 // Mixed difference of Eqs. (2.5)-(2.7) times 2 d with the upwind side chosen
 // at run time (general quadrilaterals): the upwind operands are selected,
@@ -110,38 +130,77 @@ __device__ __forceinline__ T mixed_sum(T a, T b, T cf, T f0, bool edge, T kb, T 
 // neighbours. xs = scale c_{q xi} / (2 dxi) = e_x As - e_y Bs, whose sign is
 // the upwind side along xi (it absorbs sigma: xs D = |xs| sum); along eta the
 // side is the sign of e_y (c_{q eta} = c e_y / H) and the factor is
-// Es = scale (c / H) / (2 deta).
-template <int Q, class T>
+// Es = scale (c / H) / (2 deta). As = scale c xi_x / (2 dxi) is positive, so
+// the planes with e_y = 0 have the side of e_x. With EDGE the near-wall
+// first-order form is selected by the flags; without it the far upwind
+// neighbour outside the cavity holds the linear extrapolation (a ghost value,
+// written by the caller), which gives the same difference.
+template <int Q, bool EDGE, class T>
 __device__ __forceinline__ T advect_out(T base, const T *row, int l, const T col[5], T As, T Bs,
                                         T Es, bool clo, bool chi, bool lo, bool hi, T kb, T ku3,
                                         T ku) {
   const T xs = T(ex(Q)) * As - T(ey(Q)) * Bs;
   const T f0 = col[2];
   const T fm1 = row[l - 1], fp1 = row[l + 1];
-  const bool pos = xs >= T(0);
+  const bool pos = ey(Q) == 0 ? ex(Q) > 0 : xs >= T(0);
   const T sx = mixed_sum(pos ? fp1 : fm1, pos ? fm1 : fp1, pos ? row[l - 2] : row[l + 2], f0,
-                         pos ? clo : chi, kb, ku3, ku);
+                         EDGE && (pos ? clo : chi), kb, ku3, ku);
   T out = base - fabs(xs) * sx;
   if constexpr (ey(Q) > 0)
-    out -= Es * mixed_sum(col[3], col[1], col[0], f0, lo, kb, ku3, ku);
+    out -= Es * mixed_sum(col[3], col[1], col[0], f0, EDGE && lo, kb, ku3, ku);
   else if constexpr (ey(Q) < 0)
-    out -= Es * mixed_sum(col[1], col[3], col[4], f0, hi, kb, ku3, ku);
+    out -= Es * mixed_sum(col[1], col[3], col[4], f0, EDGE && hi, kb, ku3, ku);
   return out;
 }
 
+// Writes the ghost values of a near-wall node's stencils (the EDGE = false
+// form of advect_out) into its ring (planes RS apart): `row` is the node's
+// ring row at lane l, `below` / `above` column l of the ring rows beyond the
+// bottom / lid, `wall_lo` / `wall_hi` column l of the wall rows. For a node
+// next to a side wall the row neighbour beyond the wall, for a node next to
+// the bottom / lid the column neighbour beyond it, each the linear
+// extrapolation 2 F[wall] - F[node] of the plane. Each ghost is read by this
+// thread's own stencil only (no other node takes it within the radius-2
+// stencils), so no barrier orders the write.
+template <class T, int RS>
+__device__ __forceinline__ void write_ghosts(T *row, int l, bool clo, bool chi, bool lo, bool hi,
+                                             T *below, const T *wall_lo, T *above,
+                                             const T *wall_hi) {
+  if (clo) {
+#pragma unroll
+    for (int q = 1; q < 9; ++q)
+      row[q * RS + l - 2] = T(2) * row[q * RS + l - 1] - row[q * RS + l];
+  }
+  if (chi) {
+#pragma unroll
+    for (int q = 1; q < 9; ++q)
+      row[q * RS + l + 2] = T(2) * row[q * RS + l + 1] - row[q * RS + l];
+  }
+  if (lo) {
+#pragma unroll
+    for (int q = 1; q < 9; ++q)
+      if (ey(q) > 0) below[q * RS] = T(2) * wall_lo[q * RS] - row[q * RS + l];
+  }
+  if (hi) {
+#pragma unroll
+    for (int q = 1; q < 9; ++q)
+      if (ey(q) < 0) above[q * RS] = T(2) * wall_hi[q * RS] - row[q * RS + l];
+  }
+}
+
 // out[q] for q = Q..8; ring planes are RS apart, base planes BS apart.
-template <class T, int Q, int RS, int BS>
+template <class T, int Q, int RS, int BS, bool EDGE>
 struct AdvectAll {
   __device__ __forceinline__ static void run(const T *rows, const T *const cols[5], int l, T As,
                                              T Bs, T Es, bool clo, bool chi, bool lo, bool hi,
                                              T kb, T ku3, T ku, const T *base, T out[9]) {
     const T col[5] = {cols[0][Q * RS], cols[1][Q * RS], cols[2][Q * RS], cols[3][Q * RS],
                       cols[4][Q * RS]};
-    out[Q] = advect_out<Q>(base[Q * BS], rows + Q * RS, l, col, As, Bs, Es, clo, chi, lo, hi, kb,
-                           ku3, ku);
+    out[Q] = advect_out<Q, EDGE>(base[Q * BS], rows + Q * RS, l, col, As, Bs, Es, clo, chi, lo,
+                                 hi, kb, ku3, ku);
     if constexpr (Q < 8)
-      AdvectAll<T, Q + 1, RS, BS>::run(rows, cols, l, As, Bs, Es, clo, chi, lo, hi, kb, ku3, ku,
-                                       base, out);
+      AdvectAll<T, Q + 1, RS, BS, EDGE>::run(rows, cols, l, As, Bs, Es, clo, chi, lo, hi, kb, ku3,
+                                             ku, base, out);
   }
 };
 
@@ -283,6 +342,9 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   const float *qm = GEN ? a.geo.qmet_f + 5 * cv.off : nullptr;
   auto qmet = [&](int k, int j) -> T { return qm[k * plane + int64_t(j) * pitch + cc]; };
   const T wx = T(((c == 0 || c == nx - 1) ? 0.5 : 1.0) * cv.dxi);
+  // The FP32 trapezoid stencils take their near-wall form from ghost values
+  // (write_ghosts) instead of per-plane selects on the wall flags.
+  constexpr bool GHOST = sizeof(T) == 4;
   const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
   Partial p = {0, 0, 0, 0, 0, 0, 0};
@@ -308,7 +370,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   auto prefetch = [&](int it) {
     const int r = row_of(it);
     if (lane == 0 && r >= rlo && r <= rhi && issue)
-      tma_load_box3(&S.sf[it % PF][wid][0][0], tmap, tx, r, &S.bar[it % PF][wid],
+      tma_load_box3(&S.sf[pf_slot(it)][wid][0][0], tmap, tx, r, &S.bar[pf_slot(it)][wid],
                     uint32_t(9 * 32 * sizeof(T)));
   };
   // A wait that runs out is reported in the status word; the warp then waits
@@ -320,7 +382,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   auto wait_row = [&](int it) {
     const int r = row_of(it);
     if (r >= rlo && r <= rhi) {
-      const int s = it % PF;
+      const int s = pf_slot(it);
       const bool ok = aligned && !gave_up && mbar_wait(&S.bar[s][wid], (phase >> s) & 1u);
       if (!ok && !gave_up && lane == 0) atomicOr(a.status, STATUS_TMA_TIMEOUT);
       gave_up = gave_up || !ok;
@@ -353,7 +415,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   };
   auto collide = [&](int it, T lam_prev) {
     Collided o;
-    const int s = it % PF;
+    const int s = pf_slot(it);
     T g[9];
 #pragma unroll
     for (int q = 0; q < 9; ++q) g[q] = sfme[s * SLOT + q * 32];
@@ -375,7 +437,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     }
     // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as
     // relaxation_time), or in FP32 with the pow32 opt-in
-    const T k = T(-2) / ((T(2) * lam_prev + dt) * cs2);
+    const T k = quot(T(-2), (T(2) * lam_prev + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
     if constexpr (sizeof(T) == 4) {
       // the strain rate is FP32 here: clamped in FP32, then C q^m in FP64 by
@@ -426,11 +488,11 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     const int ar = k + h;
     T Lcur = T(0);
     if (in_a(ar)) {
-      const int s = it % PF, sb = slot6(ar);
+      const int s = pf_slot(it), sb = slot6(ar);
       if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * pitch + c] = nlam;
       const T L = nlam;
       Lcur = L;
-      const T i2 = T(1) / (T(2) * L + dt);
+      const T i2 = quot(T(1), T(2) * L + dt);
       const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
       const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt) = bb
 #pragma unroll
@@ -469,8 +531,13 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         } else {
           const T As = A1 * hxs;                         // dt/2 c xi_x / (2 dxi) of row m
           const T Bs = As * xeH;                         // ... times x_eta / H
-          AdvectAll<T, 1, NC, NC>::run(&S.fb[sm][0][0], cols, l, As, Bs, Es1, clo, chi, lo, hi,
-                                       eta_b, ku3, ku, &S.fb[sm][0][l], fbar);  // Eq. (3.7)
+          if constexpr (GHOST)
+            write_ghosts<T, NC>(&S.fb[sm][0][0], l, clo, chi, lo, hi, &S.fb[slot6(-1)][0][l],
+                                &S.fb[slot6(0)][0][l], &S.fb[slot6(ny)][0][l],
+                                &S.fb[slot6(ny - 1)][0][l]);
+          AdvectAll<T, 1, NC, NC, !GHOST>::run(&S.fb[sm][0][0], cols, l, As, Bs, Es1, clo, chi, lo,
+                                               hi, eta_b, ku3, ku, &S.fb[sm][0][l],
+                                               fbar);  // Eq. (3.7)
         }
       }
       T ux, uy, P;
@@ -478,7 +545,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       T geq[9];
       equilibrium(P, ux, uy, c_, ics2, geq);
       const T L = Lprev;                                 // lambda(t) of row m
-      const T bh = dt / (T(4) * L + dt);                 // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
+      const T bh = quot(dt, T(4) * L + dt);              // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
       T fh[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = fh[q] = toward(fbar[q], geq[q], bh);
@@ -516,7 +583,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     // ---------------- stage 2: row o = k - 4 + h ----------------
     const int o = k - 4 + h;
     const bool do2 = o >= olo && o <= ohi;
-    const int sp = (it + PF - 2) % PF;               // f-hat^+ of row o (iteration it - 2)
+    const int sp = pf_slot(it + PF - 2);             // f-hat^+ of row o (iteration it - 2)
     wait_row(it + 1);                                // this warp's row of iteration it + 1
     T gnv[9];
     if (do2 && inner_c && l >= 4 && l < NC - 4) {
@@ -538,8 +605,12 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
         } else {
           const T As = A2 * fxs;                         // dt c xi_x / (2 dxi) of row o
           const T Bs = As * xeH;
-          AdvectAll<T, 1, NC, 32>::run(&S.fh[so][0][0], cols, l, As, Bs, Es2, clo, chi, lo, hi,
-                                       eta_b, ku3, ku, sfme + sp * SLOT, gnv);  // Eq. (3.6)
+          if constexpr (GHOST)
+            write_ghosts<T, NC>(&S.fh[so][0][0], l, clo, chi, lo, hi, &S.fh[slot6(-1)][0][l],
+                                &S.fh[slot6(0)][0][l], &S.fh[slot6(ny)][0][l], &S.lid[0][l]);
+          AdvectAll<T, 1, NC, 32, !GHOST>::run(&S.fh[so][0][0], cols, l, As, Bs, Es2, clo, chi, lo,
+                                               hi, eta_b, ku3, ku, sfme + sp * SLOT,
+                                               gnv);  // Eq. (3.6)
         }
       }
       if (clo || chi) {                                // values the wall columns extrapolate
