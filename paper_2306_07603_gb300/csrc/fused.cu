@@ -83,13 +83,13 @@ __device__ __forceinline__ int pf_slot(int it) { return int(unsigned(it) % unsig
 
 // a / b for the relaxation weights and the strain-rate factor, whose
 // denominators (2 lam + dt, 4 lam + dt, (2 lam + dt) c_s^2) are positive and
-// normal: a division in FP64; in FP32 the hardware reciprocal approximation
-// (__fdividef, within 2 ulp). The transforms of Eqs. (2.15)-(2.17) move F
-// towards f^eq, so an error in their weights leaves u and P unchanged and
-// reaches the populations at 2e-7 of |f^eq - F|.
-template <class T>
+// normal: with FAST in FP32 the hardware reciprocal approximation
+// (__fdividef, within 2 ulp), else a division. The transforms of
+// Eqs. (2.15)-(2.17) move F towards f^eq, so an error in their weights leaves
+// u and P unchanged and reaches the populations at 2e-7 of |f^eq - F|.
+template <bool FAST, class T>
 __device__ __forceinline__ T quot(T a, T b) {
-  if constexpr (sizeof(T) == 4)
+  if constexpr (FAST && sizeof(T) == 4)
     return __fdividef(a, b);
   else
     return a / b;
@@ -345,6 +345,10 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
   // The FP32 trapezoid stencils take their near-wall form from ghost values
   // (write_ghosts) instead of per-plane selects on the wall flags.
   constexpr bool GHOST = sizeof(T) == 4;
+  // approximate FP32 quotients (quot); the general-quadrilateral variant, whose
+  // registers are at the cap, keeps the division (the approximation's extra
+  // live values spill there)
+  constexpr bool FASTQ = !GEN;
   const T Pr = T(a.pref[task.cav]);                  // reference pressure of the deviations
 
   Partial p = {0, 0, 0, 0, 0, 0, 0};
@@ -437,7 +441,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
     }
     // Eqs. (2.12)-(2.14), (1.4): strain rate in T, power in FP64 (as
     // relaxation_time), or in FP32 with the pow32 opt-in
-    const T k = quot(T(-2), (T(2) * lam_prev + dt) * cs2);
+    const T k = quot<FASTQ>(T(-2), (T(2) * lam_prev + dt) * cs2);
     const T Sxx = k * pxx, Sxy = k * pxy, Syy = k * pyy;
     if constexpr (sizeof(T) == 4) {
       // the strain rate is FP32 here: clamped in FP32, then C q^m in FP64 by
@@ -492,7 +496,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       if (own && ar >= j0 && ar < j1) lam_out[int64_t(ar) * pitch + c] = nlam;
       const T L = nlam;
       Lcur = L;
-      const T i2 = quot(T(1), T(2) * L + dt);
+      const T i2 = quot<FASTQ>(T(1), T(2) * L + dt);
       const T bp = T(2) * dt * i2;     // Eq. (2.15): (2 lam - dt)/(2 lam + dt) = 1 - bp
       const T bb = T(1.5) * dt * i2;   // Eq. (2.16): 3 dt/(4 lam + 2 dt) = bb
 #pragma unroll
@@ -545,7 +549,7 @@ __device__ __forceinline__ void fused_task(const FusedArgs &a, FusedSmem<T, NT> 
       T geq[9];
       equilibrium(P, ux, uy, c_, ics2, geq);
       const T L = Lprev;                                 // lambda(t) of row m
-      const T bh = quot(dt, T(4) * L + dt);              // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
+      const T bh = quot<FASTQ>(dt, T(4) * L + dt);       // Eq. (2.17): 1 - bh = 4 lam/(4 lam + dt)
       T fh[9];
 #pragma unroll
       for (int q = 0; q < 9; ++q) S.fh[sm][q][l] = fh[q] = toward(fbar[q], geq[q], bh);
