@@ -57,9 +57,9 @@ extern "C" {
                             pressure every 1024 steps (a uniform pressure
                             offset is a neutral, drifting mode). The metrics,
                             the power law of Eq. (1.4) (on the FP32 strain
-                            rate), the lambda plane and all reductions are
-                            FP64 (see power_fp32 for an FP32 power). Every
-                            output includes P_ref. */
+                            rate) and all reductions are FP64 (see power_fp32
+                            for an FP32 power); the relaxation-time plane is
+                            stored in FP32. Every output includes P_ref. */
 
 /* Step kernel organisation. */
 #define IFDLBM_KERNEL_AUTO 0   /* FUSED for FP32DEV, STAGED for FP64 */
@@ -425,7 +425,8 @@ int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best);
  *   writes adj = dJ/dstate and adds the direct theta term (through the
  *   Jacobian of Eq. 3.3) to dparams.
  * ifdlbm_adjoint_step: with state_n the state before step n (Steps 2-7) and
- *   adj the adjoint of the state after it, recomputes step n and replaces adj
+ *   adj the adjoint of the state after it, recomputes step n (see
+ *   ifdlbm_adjoint_step_saved for a sweep that keeps it) and replaces adj
  *   by the adjoint of state_n, adding the step's parameter terms (n and Re
  *   through K of Eq. 2.15.1 and the exponent of Eq. 1.4; theta through the
  *   contravariant velocities of Eq. 3.4) to dparams. */
@@ -443,6 +444,29 @@ int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double 
  * cavity. */
 int ifdlbm_adjoint_seed_psi(ifdlbm_handle h, const void *state, const int *nodes, void *adj,
                             double *dparams);
+
+/* Forward intermediates of a step, kept for the adjoint sweep so that it
+ * need not recompute them (the same adjoint handles as above).
+ *
+ * ifdlbm_intermediate_bytes: bytes of one step's intermediates: f-bar^+
+ *   (Eq. 2.16), f-hat^+ (Eq. 2.15) and f(t + dt/2) (Eq. 2.17), 27 planes of
+ *   the handle's precision in its plane layout; -1 for a NULL handle.
+ * ifdlbm_save_intermediates_dev: copies the intermediates of the handle's
+ *   last ifdlbm_step into the DEVICE buffer dst (ifdlbm_intermediate_bytes
+ *   bytes, owned by the caller), on the handle's stream. The last step must
+ *   have been a single step of this handle (ifdlbm_step(h, 1)); any later
+ *   step or adjoint call overwrites the source. INVALID_ARG for a NULL
+ *   argument or a handle the adjoint does not take.
+ * ifdlbm_adjoint_step_saved: ifdlbm_adjoint_step with the forward step
+ *   given instead of recomputed: state_np1 is the state after step n
+ *   (ifdlbm_save_state_dev after the step) and inter its intermediates
+ *   (ifdlbm_save_intermediates_dev after the same step). The result is the
+ *   same bit for bit (the same kernels formed the intermediates). All
+ *   buffers are DEVICE buffers; the same errors as ifdlbm_adjoint_step. */
+int64_t ifdlbm_intermediate_bytes(ifdlbm_handle h);
+int ifdlbm_save_intermediates_dev(ifdlbm_handle h, void *dst);
+int ifdlbm_adjoint_step_saved(ifdlbm_handle h, const void *state_n, const void *state_np1,
+                              const void *inter, void *adj, double *dparams);
 
 /* Self-test of the FP64 power the FP64 form uses for Eq. (1.4): for n
  * DEVICE doubles x (finite, > 0) writes fast[k] = the library's

@@ -134,6 +134,9 @@ _SIGS = {
     "ifdlbm_adjoint_seed_energy": (C.c_int, [_H, _P, _P, _P]),
     "ifdlbm_autotune": (C.c_int, [_H, C.c_int, C.c_void_p]),
     "ifdlbm_adjoint_step": (C.c_int, [_H, _P, _P, _P]),
+    "ifdlbm_intermediate_bytes": (C.c_int64, [_H]),
+    "ifdlbm_save_intermediates_dev": (C.c_int, [_H, _P]),
+    "ifdlbm_adjoint_step_saved": (C.c_int, [_H, _P, _P, _P, _P, _P]),
     "ifdlbm_adjoint_seed_psi": (C.c_int, [_H, _P, C.c_void_p, _P, _P]),
     "ifdlbm_profile": (C.c_int, [_H, C.c_int]),
     "ifdlbm_find_eddies": (C.c_int, [C.c_int, C.c_int, ifdlbm_geometry, _P, C.c_void_p]),
@@ -391,6 +394,19 @@ def ifdlbm_adjoint_seed_psi(h, state, nodes, adj, dparams):
 
 def ifdlbm_adjoint_step(h, state_n, adj, dparams):
     return _check(load_library().ifdlbm_adjoint_step(h, _ptr(state_n), _ptr(adj), _ptr(dparams)), h)
+
+
+def ifdlbm_intermediate_bytes(h):
+    return int(load_library().ifdlbm_intermediate_bytes(h))
+
+
+def ifdlbm_save_intermediates_dev(h, dst):
+    return _check(load_library().ifdlbm_save_intermediates_dev(h, _ptr(dst)), h)
+
+
+def ifdlbm_adjoint_step_saved(h, state_n, state_np1, inter, adj, dparams):
+    return _check(load_library().ifdlbm_adjoint_step_saved(
+        h, _ptr(state_n), _ptr(state_np1), _ptr(inter), _ptr(adj), _ptr(dparams)), h)
 
 
 def ifdlbm_selftest_pow(h, x, m, fast, ref):

@@ -85,16 +85,26 @@ __device__ __forceinline__ void nee_T(double G[9], const double F[9], const CavD
   for (int i = 0; i < 9; ++i) G[i] -= cv.c * (ex(i) * ub + ey(i) * vb);
 }
 
+// The distinct coefficients of the mixed difference of Eq. (2.5) (times 2 d)
+// for blend eta, formed once per thread: eta, o = 1 - eta, 2 o, 3 o,
+// eta + 2 o and eta + 4 o.
+struct Blend {
+  double e, o, o2, o3, e2, e4;
+};
+__device__ __forceinline__ Blend make_blend(double eta) {
+  const double o = 1.0 - eta;
+  return {eta, o, 2.0 * o, 3.0 * o, eta + 2.0 * o, eta + 4.0 * o};
+}
+
 // Coefficient of F[x + k] in the mixed difference of Eq. (2.5) at node x
 // (times 2 d), for the upwind side `pos` and the near-wall flags lo / hi.
-__device__ __forceinline__ double wmix(int k, bool pos, bool lo, bool hi, double eta) {
-  const double o = 1.0 - eta;
+__device__ __forceinline__ double wmix(int k, bool pos, bool lo, bool hi, const Blend &b) {
   if (pos) {
-    if (lo) return k == -1 ? -eta - 2.0 * o : (k == 0 ? 2.0 * o : (k == 1 ? eta : 0.0));
-    return k == -2 ? o : (k == -1 ? -eta - 4.0 * o : (k == 0 ? 3.0 * o : (k == 1 ? eta : 0.0)));
+    if (lo) return k == -1 ? -b.e2 : (k == 0 ? b.o2 : (k == 1 ? b.e : 0.0));
+    return k == -2 ? b.o : (k == -1 ? -b.e4 : (k == 0 ? b.o3 : (k == 1 ? b.e : 0.0)));
   }
-  if (hi) return k == -1 ? -eta : (k == 0 ? -2.0 * o : (k == 1 ? eta + 2.0 * o : 0.0));
-  return k == -1 ? -eta : (k == 0 ? -3.0 * o : (k == 1 ? eta + 4.0 * o : (k == 2 ? -o : 0.0)));
+  if (hi) return k == -1 ? -b.e : (k == 0 ? -b.o2 : (k == 1 ? b.e2 : 0.0));
+  return k == -1 ? -b.e : (k == 0 ? -b.o3 : (k == 1 ? b.e4 : (k == 2 ? -b.o : 0.0)));
 }
 
 __device__ __forceinline__ double cxi_at(const CavDev &cv, const Geo &g, int q, int i, int j) {
@@ -122,29 +132,38 @@ __device__ __forceinline__ double dxi_at(const CavDev &cv, const Geo &g, const d
 }
 
 // Gather of the transposed advection: sum over interior x on the xi and eta
-// lines through y of Gb_q(x) dA_q(x)/dF_q(y).
+// lines through y of Gb_q(x) dA_q(x)/dF_q(y). c_{q xi}(x) is formed as in
+// cxi_at (the row's metric c xi_x loaded once), so that its sign, which picks
+// the upwind side, is the forward step's; the constant factors 1 / (2 dxi)
+// and c_{q eta} / (2 deta) are applied to each line's sum.
 __device__ __forceinline__ double advect_T(const CavDev &cv, const Geo &g, const double *Gb, int q,
-                                           int i, int j) {
+                                           int i, int j, const Blend &bl) {
   double acc = 0.0;
-  const double ceta = double(ey(q)) * cv.c / cv.H;
   if (j >= 1 && j <= cv.ny - 2) {
+    const double A = cv.c * g.xix[cv.goff + j];
+    const double *row = Gb + int64_t(j) * cv.pitch;
+    double sx = 0.0;
 #pragma unroll
     for (int k = -2; k <= 2; ++k) {
       const int xi = i - k;  // F(y) = F(x + k)
       if (xi < 1 || xi > cv.nx - 2) continue;
-      const double cx = cxi_at(cv, g, q, xi, j);
-      const double w = wmix(k, cx >= 0.0, xi == 1, xi == cv.nx - 2, cv.eta_b);
-      if (w != 0.0) acc += Gb[int64_t(j) * cv.pitch + xi] * cx * w * cv.inv2dxi;
+      const double cx = ex(q) * A - ey(q) * A * g.xeH[cv.goff + xi];
+      const double w = wmix(k, cx >= 0.0, xi == 1, xi == cv.nx - 2, bl);
+      if (w != 0.0) sx += row[xi] * cx * w;
     }
+    acc = sx * cv.inv2dxi;
   }
+  const double ceta = double(ey(q)) * cv.c / cv.H;
   if (i >= 1 && i <= cv.nx - 2 && ceta != 0.0) {
+    double se = 0.0;
 #pragma unroll
     for (int k = -2; k <= 2; ++k) {
       const int yj = j - k;
       if (yj < 1 || yj > cv.ny - 2) continue;
-      const double w = wmix(k, ceta >= 0.0, yj == 1, yj == cv.ny - 2, cv.eta_b);
-      if (w != 0.0) acc += Gb[int64_t(yj) * cv.pitch + i] * ceta * w * cv.inv2deta;
+      const double w = wmix(k, ceta >= 0.0, yj == 1, yj == cv.ny - 2, bl);
+      if (w != 0.0) se += Gb[int64_t(yj) * cv.pitch + i] * w;
     }
+    acc += se * (ceta * cv.inv2deta);
   }
   return acc;
 }
@@ -303,11 +322,12 @@ __global__ void k_adj3_stencil(AdjArgs a) {
     const double *fh = a.fh + 9 * cv.off;
     double *fhb = a.fhb + 9 * cv.off;
     fhb[node] = 0.0;
-#pragma unroll 1
+    const Blend bl = make_blend(cv.eta_b);
+#pragma unroll
     for (int q = 1; q < 9; ++q)
-      fhb[q * cv.plane + node] = -cv.dt * advect_T(cv, a.geo, ag + q * cv.plane, q, r.i, r.j);
+      fhb[q * cv.plane + node] = -cv.dt * advect_T(cv, a.geo, ag + q * cv.plane, q, r.i, r.j, bl);
     if (interior(cv, r.i, r.j)) {
-#pragma unroll 1
+#pragma unroll
       for (int q = 1; q < 9; ++q) {
         const double gb = ag[q * cv.plane + node];
         dth += -cv.dt * gb * dcxi_dtheta(cv, a.geo, q, r.i, r.j) *
@@ -351,7 +371,7 @@ __global__ void k_adj2_point(AdjArgs a) {
   double fbar[9];
   fbar[0] = fb[node];
   const double hdt = 0.5 * cv.dt;
-#pragma unroll 1
+#pragma unroll
   for (int q = 1; q < 9; ++q) {
     const double cx = cxi_at(cv, a.geo, q, r.i, r.j);
     const double ce = double(ey(q)) * cv.c / cv.H;
@@ -397,12 +417,13 @@ __global__ void k_adj2_stencil(AdjArgs a) {
     double *fbb = a.fbb + 9 * cv.off;
     const double hdt = 0.5 * cv.dt;
     fbb[node] = fbarb[node];
-#pragma unroll 1
+    const Blend bl = make_blend(cv.eta_b);
+#pragma unroll
     for (int q = 1; q < 9; ++q)
-      fbb[q * cv.plane + node] =
-          fbarb[q * cv.plane + node] - hdt * advect_T(cv, a.geo, fbarb + q * cv.plane, q, r.i, r.j);
+      fbb[q * cv.plane + node] = fbarb[q * cv.plane + node] -
+                                 hdt * advect_T(cv, a.geo, fbarb + q * cv.plane, q, r.i, r.j, bl);
     if (interior(cv, r.i, r.j)) {
-#pragma unroll 1
+#pragma unroll
       for (int q = 1; q < 9; ++q)
         dth += -hdt * fbarb[q * cv.plane + node] * dcxi_dtheta(cv, a.geo, q, r.i, r.j) *
                dxi_at(cv, a.geo, fb + q * cv.plane, q, r.i, r.j);

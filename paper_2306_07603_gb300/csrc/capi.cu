@@ -1390,6 +1390,51 @@ int ifdlbm_adjoint_step(ifdlbm_handle h, const void *state_n, void *adj, double 
   return IFDLBM_OK;
 }
 
+int64_t ifdlbm_intermediate_bytes(ifdlbm_handle h) {
+  if (!h) return -1;
+  const size_t tsize = h->precision == IFDLBM_FP64 ? sizeof(double) : sizeof(float);
+  return int64_t(27 * h->total_plane * tsize);
+}
+
+int ifdlbm_save_intermediates_dev(ifdlbm_handle h, void *dst) {
+  if (!h || !dst) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad handle or dst");
+  cudaSetDevice(h->device);
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  // the staged kernels' scratch planes hold the last step's f-bar^+, f-hat^+
+  // and f(t + dt/2), in the order the adjoint reads them
+  const size_t P9 = 9 * size_t(h->total_plane) * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  const void *src[3] = {h->b.fb, h->b.fp, h->b.fh};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    e = cudaMemcpyAsync((char *)dst + k * P9, src[k], P9, cudaMemcpyDeviceToDevice, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "save_intermediates_dev");
+  return IFDLBM_OK;
+}
+
+int ifdlbm_adjoint_step_saved(ifdlbm_handle h, const void *state_n, const void *state_np1,
+                              const void *inter, void *adj, double *dparams) {
+  if (!h || !state_n || !state_np1 || !inter || !adj || !dparams)
+    return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
+  cudaSetDevice(h->device);
+  int rc = adjoint_ready(h);
+  if (rc) return rc;
+  // step n's outputs (state n + 1: its populations and lambda(t), which the
+  // step stores as the next step's lagged value) and intermediates, as saved
+  const int64_t n9 = 9 * h->total_plane;
+  ifd::AdjArgs a = adj_args(h, state_n, adj);
+  a.gn = (const double *)state_np1;
+  a.lam = (const double *)state_np1 + n9;
+  a.fb = (const double *)inter;
+  a.fp = (const double *)inter + n9;
+  a.fh = (const double *)inter + 2 * n9;
+  ifd::launch_adjoint_step(a, h->ntiles, h->ncav, dparams, h->stream);
+  g_launches += 9;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(h, e, "adjoint step (saved)");
+  return IFDLBM_OK;
+}
+
 int ifdlbm_autotune(ifdlbm_handle h, int trial_steps, ifdlbm_tuning *best) {
   if (!h || !best || trial_steps < 1) return fail(h, IFDLBM_ERR_INVALID_ARG, "bad arguments");
   if (h->kernel != IFDLBM_KERNEL_FUSED)

@@ -93,7 +93,7 @@ def _gpu_energy(n, Re, th, nx, ny, T):
     return e
 
 
-@pytest.mark.parametrize("every", [7, 40])
+@pytest.mark.parametrize("every", [1, 7, 40])
 def test_energy_gradient_matches_central_differences(every):
     from paper_2306_07603_gb300.adjoint import energy_and_gradient
     x = [0.75, 400.0, 60.0]
@@ -153,7 +153,7 @@ def _gpu_psimin(n, Re, th, nx, ny, T):
     return float(psi[1:-1, 1:-1].min())
 
 
-@pytest.mark.parametrize("every", [7, 40])
+@pytest.mark.parametrize("every", [1, 7, 40])
 def test_psi_min_gradient_matches_central_differences(every):
     from paper_2306_07603_gb300.adjoint import objective_and_gradient
     x = [0.75, 400.0, 60.0]
@@ -209,3 +209,61 @@ def test_adjoint_seed_psi_rejects_nodes_outside_the_cavity():
     with pytest.raises(capi.IfdlbmError):
         capi.ifdlbm_adjoint_seed_psi(s.h, buf, [(17, 3)], adj, dp)
     s.close()
+
+
+def test_adjoint_step_saved_equals_recomputing_step():
+    """ifdlbm_adjoint_step_saved, fed the state after each step and the step's
+    intermediates as ifdlbm_step left them, gives the adjoint and the parameter
+    terms of ifdlbm_adjoint_step (which forms the step again) bit for bit, over
+    a reverse sweep of five steps from an oracle-developed state."""
+    import torch
+
+    from paper_2306_07603_gb300 import capi
+    from paper_2306_07603_gb300.solver import Solver, cavity
+    from paper_2306_07603_gb300.workloads import smooth_noise
+
+    nx, ny, n = 37, 29, 0.75
+    run = O.cavity_run(nx, 400.0, n, theta_deg=60.0, ny=ny, dt_mode="grid")
+    run.advance(40)
+    s = Solver([cavity(nx, ny, 400.0, n, theta_deg=60.0)], precision="fp64", kernel="staged",
+               dt_mode="grid")
+    states = [_dev_state(s, run.fhat.copy(), run.lam.copy())]
+    nb = capi.ifdlbm_intermediate_bytes(s.h)
+    assert nb == 27 * (capi.ifdlbm_state_bytes(s.h) - 8) // 10
+    inter = []
+    for _ in range(5):
+        s.step(1)
+        st = torch.empty_like(states[0])
+        it = torch.empty(nb // 8, dtype=torch.float64, device="cuda")
+        capi.ifdlbm_save_state_dev(s.h, st)
+        capi.ifdlbm_save_intermediates_dev(s.h, it)
+        states.append(st)
+        inter.append(it)
+    seed = smooth_noise((9, ny, nx), seed=5)
+    w = _dev_state(s, seed + O.OMEGA[:, None, None], smooth_noise((ny, nx), seed=6))
+    a_re, a_sv = w.clone(), w.clone()
+    d_re = torch.zeros(3, dtype=torch.float64, device="cuda")
+    d_sv = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for k in range(4, -1, -1):
+        capi.ifdlbm_adjoint_step(s.h, states[k], a_re, d_re)
+        capi.ifdlbm_adjoint_step_saved(s.h, states[k], states[k + 1], inter[k], a_sv, d_sv)
+    s.sync()
+    assert torch.equal(a_re, a_sv)
+    assert torch.equal(d_re, d_sv)
+    assert float(d_re.abs().sum()) > 0.0
+    with pytest.raises(capi.IfdlbmError):
+        capi.ifdlbm_adjoint_step_saved(s.h, states[0], None, inter[0], a_sv, d_sv)
+    with pytest.raises(capi.IfdlbmError):
+        capi.ifdlbm_save_intermediates_dev(s.h, None)
+    s.close()
+
+
+def test_gradient_does_not_depend_on_the_checkpoint_interval():
+    """Every checkpointing of the sweep feeds the adjoint the same states and
+    intermediates (recomputed from checkpoints, or kept by the forward pass
+    with every = 1), so the gradients agree bit for bit."""
+    from paper_2306_07603_gb300.adjoint import energy_and_gradient
+    x = [0.75, 400.0, 60.0]
+    ref = energy_and_gradient(*x, 33, 29, 40, every=1)
+    for every in (3, 40, 100):
+        assert energy_and_gradient(*x, 33, 29, 40, every=every) == ref
