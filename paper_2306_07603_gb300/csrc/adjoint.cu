@@ -112,23 +112,35 @@ __device__ __forceinline__ double cxi_at(const CavDev &cv, const Geo &g, int q, 
   return ex(q) * A - ey(q) * A * g.xeH[cv.goff + i];
 }
 
-// d c_{q xi} / d theta_deg at node (i, j): x_xi = L + 2 H cot eta, x_eta = H cot (2 xi - 1).
-__device__ __forceinline__ double dcxi_dtheta(const CavDev &cv, const Geo &g, int q, int i, int j) {
-  const double A = cv.c * g.xix[cv.goff + j];
-  const double xi = i * cv.dxi, eta = j * cv.deta;
-  const double dcot = -A * ey(q) * (2.0 * xi - 1.0) -
-                      A * (ex(q) - ey(q) * g.xeH[cv.goff + i]) * 2.0 * cv.H * eta * g.xix[cv.goff + j];
-  return dcot * cv.dcot;
+// Per-node terms of c_{q xi} and of its theta derivative, formed once for all
+// planes: with A = c xi_x and x_eta / H of the node, c_{q xi} = e_x A - e_y A
+// x_eta / H (as cxi_at), and, through x_xi = L + 2 H cot eta and x_eta = H cot
+// (2 xi - 1), d c_{q xi} / d theta_deg = e_y t1 - e_x t2 with
+// t1 = (-A (2 xi - 1) + A x_eta/H K) dcot, t2 = A K dcot, K = 2 H eta xi_x.
+struct NodeXi {
+  double A, xe, t1, t2;
+  __device__ __forceinline__ double cxi(int q) const { return ex(q) * A - ey(q) * A * xe; }
+  __device__ __forceinline__ double dcxi(int q) const { return ey(q) * t1 - ex(q) * t2; }
+};
+__device__ __forceinline__ NodeXi node_xi(const CavDev &cv, const Geo &g, int i, int j) {
+  const double xix = g.xix[cv.goff + j];
+  const double A = cv.c * xix, xe = g.xeH[cv.goff + i];
+  const double K = 2.0 * cv.H * (j * cv.deta) * xix;
+  return {A, xe, (-A * (2.0 * (i * cv.dxi) - 1.0) + A * xe * K) * cv.dcot, A * K * cv.dcot};
 }
 
-// D_xi F_q at interior node (i, j) of plane F (as in the forward kernels).
-__device__ __forceinline__ double dxi_at(const CavDev &cv, const Geo &g, const double *F, int q,
-                                         int i, int j) {
+// D_xi F_q at interior node (i, j) of plane F (as in the forward kernels), on
+// the upwind side of c_{q xi} = cx.
+__device__ __forceinline__ double dxi_with(const CavDev &cv, const double *F, double cx, int i,
+                                           int j) {
   const int64_t node = int64_t(j) * cv.pitch + i;
   const int im2 = i >= 2 ? -2 : -1, ip2 = i <= cv.nx - 3 ? 2 : 1;
-  const bool pos = cxi_at(cv, g, q, i, j) >= 0.0;
-  return dmix2(F[node + im2], F[node - 1], F[node], F[node + 1], F[node + ip2], pos, i == 1,
+  return dmix2(F[node + im2], F[node - 1], F[node], F[node + 1], F[node + ip2], cx >= 0.0, i == 1,
                i == cv.nx - 2, cv.eta_b) * cv.inv2dxi;
+}
+__device__ __forceinline__ double dxi_at(const CavDev &cv, const Geo &g, const double *F, int q,
+                                         int i, int j) {
+  return dxi_with(cv, F, cxi_at(cv, g, q, i, j), i, j);
 }
 
 // Gather of the transposed advection: sum over interior x on the xi and eta
@@ -327,11 +339,11 @@ __global__ void k_adj3_stencil(AdjArgs a) {
     for (int q = 1; q < 9; ++q)
       fhb[q * cv.plane + node] = -cv.dt * advect_T(cv, a.geo, ag + q * cv.plane, q, r.i, r.j, bl);
     if (interior(cv, r.i, r.j)) {
+      const NodeXi nm = node_xi(cv, a.geo, r.i, r.j);
 #pragma unroll
       for (int q = 1; q < 9; ++q) {
         const double gb = ag[q * cv.plane + node];
-        dth += -cv.dt * gb * dcxi_dtheta(cv, a.geo, q, r.i, r.j) *
-               dxi_at(cv, a.geo, fh + q * cv.plane, q, r.i, r.j);
+        dth += -cv.dt * gb * nm.dcxi(q) * dxi_with(cv, fh + q * cv.plane, nm.cxi(q), r.i, r.j);
       }
     }
   }
@@ -423,10 +435,11 @@ __global__ void k_adj2_stencil(AdjArgs a) {
       fbb[q * cv.plane + node] = fbarb[q * cv.plane + node] -
                                  hdt * advect_T(cv, a.geo, fbarb + q * cv.plane, q, r.i, r.j, bl);
     if (interior(cv, r.i, r.j)) {
+      const NodeXi nm = node_xi(cv, a.geo, r.i, r.j);
 #pragma unroll
       for (int q = 1; q < 9; ++q)
-        dth += -hdt * fbarb[q * cv.plane + node] * dcxi_dtheta(cv, a.geo, q, r.i, r.j) *
-               dxi_at(cv, a.geo, fb + q * cv.plane, q, r.i, r.j);
+        dth += -hdt * fbarb[q * cv.plane + node] * nm.dcxi(q) *
+               dxi_with(cv, fb + q * cv.plane, nm.cxi(q), r.i, r.j);
     }
   }
   tile_sum3(0.0, 0.0, dth, a.ppart, 1);
