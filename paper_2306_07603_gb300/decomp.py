@@ -163,3 +163,50 @@ class StripStepper:
         out = state.clone()
         out[:, self.s.own, :] = new[:, self.s.own, :]
         return out
+
+
+def trapezoid_strip_corners(L: float, H: float, theta_deg: float, ny: int, p0: int, p1: int):
+    """Corners (bottom-left, bottom-right, top-left, top-right) of the rows
+    [p0, p1) of an ny-row trapezoid cavity. The map of Eq. (3.8.1), with the
+    lid's left end at x = 0, x = H cot(theta) + L xi + H cot(theta) (2 xi - 1)
+    eta, y = H eta, is bilinear in (xi, eta), so the strip is the
+    quadrilateral of these corners, and its own uniform grid of p1 - p0 rows
+    falls on the cavity's rows p0..p1-1."""
+    import math
+    cot = 0.0 if theta_deg == 90.0 else 1.0 / math.tan(math.radians(theta_deg))
+
+    def xy(xi, eta):
+        return (H * cot + L * xi + H * cot * (2.0 * xi - 1.0) * eta, H * eta)
+
+    e0, e1 = p0 / (ny - 1), (p1 - 1) / (ny - 1)
+    return (xy(0.0, e0), xy(1.0, e0), xy(0.0, e1), xy(1.0, e1))
+
+
+class LibraryStripStep:
+    """`local_step` of StripStepper on the CUDA library: the padded strip of
+    rows [p0, p1) of a trapezoid cavity, held by a handle of its own as the
+    quadrilateral cavity of its rows (trapezoid_strip_corners), FP64 on the
+    staged kernels, at the undivided cavity's time step `dt` and reference
+    length H. The handle applies its wall rule and near-wall differences at
+    all four edges of the strip; at a strip edge inside the cavity those land
+    on halo rows, which StripStepper discards. The state crosses the host
+    (set_state / get_state: the nine f-hat planes and lambda), so that the
+    exchange can run over any torch.distributed backend."""
+
+    def __init__(self, strip: Strip, nx: int, Re: float, n: float, theta_deg: float, dt: float,
+                 U_lid: float = 0.1, L: float = 1.0, H: float = 1.0, **options):
+        from .solver import Solver, quad_cavity
+        corners = trapezoid_strip_corners(L, H, theta_deg, strip.ny, strip.p0, strip.p1)
+        self.solver = Solver([quad_cavity(nx, strip.rows, corners, Re, n, U_lid=U_lid, H=H)],
+                             precision="fp64", kernel="staged", dt=dt, **options)
+
+    def __call__(self, state: torch.Tensor) -> torch.Tensor:
+        import numpy as np
+        s = state.detach().to("cpu", torch.float64).numpy()
+        self.solver.set_state(0, np.ascontiguousarray(s[:9]), np.ascontiguousarray(s[9]))
+        self.solver.step(1)
+        f, lam = self.solver.get_state(0)
+        return torch.from_numpy(np.concatenate([f, lam[None]])).to(state.device)
+
+    def close(self):
+        self.solver.close()

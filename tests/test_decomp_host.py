@@ -146,3 +146,18 @@ def test_a_halo_of_two_rows_is_not_enough():
         g = _strip_grid(run.g, s)
         f, _ = O.step(full[:9, s.p0:s.p1], full[9, s.p0:s.p1], g, run.prm)
         assert np.array_equal(f[:, s.own], ref[:, s.r0:s.r1]) == equal, halo
+
+
+@pytest.mark.parametrize("theta", [45.0, 60.0, 90.0])
+def test_strip_corners_are_the_cavity_grid_points(theta):
+    """trapezoid_strip_corners: the corners of rows [p0, p1) are the cavity's
+    grid points (oracle map of Eq. 3.8.1) at those rows' ends."""
+    import oracle as O
+    from paper_2306_07603_gb300 import decomp
+    run = O.cavity_run(N, RE, NPL, theta_deg=theta, ny=29)
+    g = run.g
+    for p0, p1 in ((0, 29), (0, 12), (7, 19), (15, 29)):
+        c = decomp.trapezoid_strip_corners(1.0, 1.0, theta, 29, p0, p1)
+        want = ((g.x[p0, 0], g.y[p0, 0]), (g.x[p0, -1], g.y[p0, -1]),
+                (g.x[p1 - 1, 0], g.y[p1 - 1, 0]), (g.x[p1 - 1, -1], g.y[p1 - 1, -1]))
+        assert np.allclose(np.array(c), np.array(want), rtol=0, atol=1e-14), (p0, p1, c, want)
