@@ -377,29 +377,26 @@ __global__ void k_adj2_point(AdjArgs a) {
     a.lamb2[cv.off + node] = 0.0;
     return;
   }
-  const double *fb = a.fb + 9 * cv.off;
+  const double *fh = a.fh + 9 * cv.off;
   const double *fhb = a.fhb + 9 * cv.off;
   const double lam = a.lam[cv.off + node];
-  double fbar[9];
-  fbar[0] = fb[node];
-  const double hdt = 0.5 * cv.dt;
+  // f-bar(t + dt/2) of the node from the stored f(t + dt/2): Eq. (2.17),
+  // f = f-bar + bh (f^eq - f-bar), keeps u and P, so f^eq is that of f and
+  // f-bar = (f - bh f^eq) / ah, pointwise (no second evaluation of the
+  // half step's stencil)
+  double fhv[9];
 #pragma unroll
-  for (int q = 1; q < 9; ++q) {
-    const double cx = cxi_at(cv, a.geo, q, r.i, r.j);
-    const double ce = double(ey(q)) * cv.c / cv.H;
-    const double *F = fb + q * cv.plane;
-    const int jm2 = r.j >= 2 ? -2 : -1, jp2 = r.j <= cv.ny - 3 ? 2 : 1;
-    const int64_t p = cv.pitch;
-    const double dy = dmix2(F[node + jm2 * p], F[node - p], F[node], F[node + p], F[node + jp2 * p],
-                            ce >= 0.0, r.j == 1, r.j == cv.ny - 2, cv.eta_b) * cv.inv2deta;
-    fbar[q] = F[node] - hdt * (cx * dxi_at(cv, a.geo, F, q, r.i, r.j) + ce * dy);
-  }
+  for (int q = 0; q < 9; ++q) fhv[q] = fh[q * cv.plane + node];
   double ux, uy, P;
-  moments(fbar, cv.c, cv.cs2, ux, uy, P);
+  moments(fhv, cv.c, cv.cs2, ux, uy, P);
   double geq[9];
   equilibrium(P, ux, uy, cv.c, cv.inv_cs2, geq);
   const double i4 = 1.0 / (4.0 * lam + cv.dt);
   const double ah = 4.0 * lam * i4, bh = cv.dt * i4;
+  const double iah = (4.0 * lam + cv.dt) / (4.0 * lam);  // 1 / ah
+  double fbar[9];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) fbar[q] = (fhv[q] - bh * geq[q]) * iah;
   double hb[9], eb[9], out[9];
   double lb = 0.0;
 #pragma unroll
