@@ -104,6 +104,11 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.ifdlbm_sync(None) == capi.IFDLBM_ERR_INVALID_ARG
     assert lib.ifdlbm_destroy(None) == capi.IFDLBM_OK
     assert lib.ifdlbm_state_bytes(None) == -1
+    # the adjoint sweep's intermediates
+    assert lib.ifdlbm_intermediate_bytes(None) == -1
+    assert lib.ifdlbm_save_intermediates_dev(None, None) == capi.IFDLBM_ERR_INVALID_ARG
+    assert lib.ifdlbm_adjoint_step_saved(None, None, None, None, None, None) == \
+        capi.IFDLBM_ERR_INVALID_ARG
 
 
 SKEW = ((0.1, -0.05), (1.3, 0.12), (-0.2, 0.9), (1.05, 1.1))
